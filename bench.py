@@ -1,0 +1,322 @@
+#!/usr/bin/env python3
+"""Benchmark of the decomposed sequential sweep on one GB300.
+
+Workload: 2D variable-coefficient diffusion, 5-point, 2048 x 2048 cells,
+alpha = box5x5(exp(N(0,1))) (seeded), b ~ U[-1,1], fp64; the paper's decomposed
+ILU(0) over 16 x 16 subdomains as the preconditioner of BiCGSTAB, solved to
+||b - A x|| / ||b|| <= 1e-8 from x = 0. One step = ilu0_factor + krylov_solve.
+
+Metric: Gcell-updates/s (cell updates of every sweep kernel in the step: the
+factor sweep and the two sweeps of every ILU(0) apply, N cells each, over the
+wall time of the whole step), with solves/s and p50/p99 solve latency beside
+it, and the roofline of the sweep kernel (algorithmic bytes / device time of
+its launches, from CUDA events on the handle's stream).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own copy (replicas; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIDE, SUB = 2048, 16
+WORKLOAD = "varcoef2d-2048x2048-5pt-fp64-ilu0-bicgstab-16x16"
+METRIC = "Gcell-updates/s per sweep (% HBM peak); solves/s and p99 latency at rel-res 1e-8"
+SWEEP_SRC = os.path.join(ROOT, "paper_1008_3699_gb300", "csrc", "sweep2d.cu")
+PROFILE = os.path.join(ROOT, "profiles", "sweep2d_ilu0_varcoef2048.md")
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic():
+    """dram bytes per launch of the sweep kernel from the committed ncu summary,
+    only if the kernel source is unchanged since the counters were taken."""
+    if not os.path.exists(PROFILE):
+        return None
+    text = open(PROFILE).read()
+    m = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+    if not m or not t:
+        return None
+    sha = hashlib.sha256(open(SWEEP_SRC, "rb").read()).hexdigest()
+    return float(t.group(1)) if sha == m.group(1) else None
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.proc = None
+        self.lines = []
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(problem, iters=6):
+    """The oracle as it stands, on one host core: the ILU(0) factor and a bounded
+    number of BiCGSTAB iterations of the same workload."""
+    import oracle
+    oracle.build()
+    pb = oracle.Problem(2, problem["n"], 5, problem["diags"], problem["sub"])
+    t0 = time.perf_counter()
+    pb.ilu0_factor(oracle.DECOMPOSED)
+    _, info = pb.solve(oracle.BICGSTAB, oracle.PREC_ILU0, oracle.DECOMPOSED, 1.0, 1e-8, iters, problem["b"])
+    dt = time.perf_counter() - t0
+    N = problem["n"][0] * problem["n"][1]
+    sweeps = 1 + 4 * info["iters"]  # factor + two applies (two sweeps each) per iteration
+    return {"value": N * sweeps / dt / 1e9, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"ILU(0) factor + {info['iters']} BiCGSTAB iterations of the 2048^2 workload "
+                      f"({sweeps} sweeps, {dt:.1f} s, 1 thread)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1008_3699_gb300 import workloads as W
+    problem = W.varcoef2d_problem(N_SIDE, SUB)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(problem, iters=2)
+        if k >= args.warmup:
+            vals.append(r)
+    v = statistics.median(x["value"] for x in vals)
+    N = N_SIDE * N_SIDE
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "Gcell-updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [N_SIDE, N_SIDE], "subdomains": [SUB, SUB]},
+        "cpu_baseline": {"value": v, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": vals[0]["sample"]},
+        "e2e": {"value": v, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "ms_per_step": 2 * 1e3 * N / (v * 1e9) if v else None,
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-natural", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    from paper_1008_3699_gb300 import build as nd_build
+    from paper_1008_3699_gb300 import ndiag as nd
+    from paper_1008_3699_gb300 import workloads as W
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus and "RANK" in os.environ:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE {world}")
+    nd_build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    problem = W.varcoef2d_problem(N_SIDE, SUB)
+    N = N_SIDE * N_SIDE
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(problem)  # host only, before the GPU work
+
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h = nd.NDiag(2, problem["n"], 5, problem["diags"], problem["sub"], "fp64", stream=stream)
+        b = torch.tensor(problem["b"], device="cuda")
+        x = torch.zeros(N, dtype=torch.float64, device="cuda")
+
+        def step():
+            h.ilu0_factor(nd.DECOMPOSED)
+            x.zero_()
+            return h.solve(nd.BICGSTAB, nd.PREC_ILU0, b, x, rtol=1e-8, maxit=20000)
+
+        for _ in range(args.warmup):
+            info = step()
+        uuid = None
+        try:
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+        except Exception:
+            pass
+        clocks = Clocks(uuid)
+        barrier()
+        torch.cuda.synchronize()
+        h.profile(True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev[0].record(stream)
+        infos = []
+        for k in range(args.steps):
+            infos.append(step())
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop()
+        cnt = h.counters()
+        lat = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+        total_ms = ev[0].elapsed_time(ev[-1])
+        tmax = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        updates = torch.tensor([float(N) * cnt["sweep_launches"]], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+            dist.all_reduce(updates, op=dist.ReduceOp.SUM)
+        total_ms = float(tmax.item())
+        value = float(updates.item()) / (total_ms / 1e3) / 1e9
+
+        # end to end through the C ABI with pinned host buffers
+        hb = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        hb.copy_(torch.from_numpy(problem["b"]))
+        hx = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        hd = torch.empty(problem["diags"].shape, dtype=torch.float64, pin_memory=True)
+        hd.copy_(torch.from_numpy(problem["diags"]))
+        hb_np, hx_np, hd_np = hb.numpy(), hx.numpy(), hd.numpy()
+        e2e_updates, e2e_s = 0.0, 0.0
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = nd.NDiag(2, problem["n"], 5, hd_np, problem["sub"], "fp64", stream=stream)
+            g.profile(False)
+            g.ilu0_factor(nd.DECOMPOSED)
+            hx_np[:] = 0.0
+            g.solve(nd.BICGSTAB, nd.PREC_ILU0, hb_np, hx_np, rtol=1e-8, maxit=20000)
+            c2 = g.counters()
+            g.close()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if k > 0:  # first one warms the allocator
+                e2e_updates += float(N) * c2["sweep_launches"]
+                e2e_s += dt
+        e2e_val = torch.tensor([e2e_updates / e2e_s / 1e9 * world], dtype=torch.float64, device="cuda")
+
+        natural = None
+        if not args.no_natural and rank == 0:
+            hn = nd.NDiag(2, problem["n"], 5, problem["diags"], (1, 1), "fp64", stream=stream)
+            hn.ilu0_factor(nd.NATURAL)
+            xn = torch.zeros(N, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ni = hn.solve(nd.BICGSTAB, nd.PREC_ILU0, b, xn, rtol=1e-8, maxit=20000, mode=nd.NATURAL,
+                          raise_on_noconv=False)
+            torch.cuda.synchronize()
+            natural = {"iters": ni["iters"], "relres": ni["relres"], "seconds": time.perf_counter() - t0}
+            hn.close()
+
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    achieved = cnt["sweep_bytes"] / (cnt["sweep_ms"] / 1e3) / 1e9 if cnt["sweep_ms"] > 0 else None
+    lat_sorted = sorted(lat)
+    p = lambda q: lat_sorted[min(len(lat_sorted) - 1, int(round(q * (len(lat_sorted) - 1))))]
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "Gcell-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [N_SIDE, N_SIDE], "subdomains": [SUB, SUB],
+                   "method": "BiCGSTAB + decomposed ILU(0)", "rtol": 1e-8, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (matrix 168 MB + 9 vectors of 34 MB vs 129 MB L2)"},
+        "solves_per_s": world * args.steps / (total_ms / 1e3),
+        "latency_ms": {"p50": p(0.5), "p99": p(0.99)},
+        "iters": [i["iters"] for i in infos],
+        "relres": max(i["relres"] for i in infos),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": kernel_traffic(),
+                     "kernel": "sweep2d_kernel (ILU(0) apply and factor sweeps)",
+                     "peak_kind": peak_kind, "sweep_launches": cnt["sweep_launches"],
+                     "sweep_ms": cnt["sweep_ms"], "sweep_bytes": cnt["sweep_bytes"]},
+        "sweep_share_of_step": cnt["sweep_ms"] / total_ms if total_ms else None,
+        "gpu_launches": cnt["launches"],
+        "e2e": {"value": float(e2e_val.item()), "unit": "Gcell-updates/s",
+                "h2d_bytes_per_step": int(hd_np.nbytes + hb_np.nbytes + hx_np.nbytes),
+                "d2h_bytes_per_step": int(hx_np.nbytes)},
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "natural_ilu0": natural,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

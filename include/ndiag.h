@@ -1,0 +1,207 @@
+/*
+ * ndiag.h -- C ABI of the GB300 library for the decomposed ("parallel")
+ * sequential sweep on structured n-diagonal matrices:
+ *   R. Tavakoli, "Parallelizing sequential sweeping on structured grids --
+ *   fully parallel SOR/ILU preconditioners for structured n-diagonal
+ *   matrices", arXiv 1008.3699.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an ndiag_status and never aborts. NDIAG_OK = 0.
+ *  - Vectors are in natural cell order (x fastest, then y, then z).
+ *  - "device" pointers are CUDA device pointers on the handle's device, owned
+ *    by the caller; the library neither frees nor retains them after the call.
+ *  - The library owns what it copies at create time (diagonals, scaled
+ *    coefficients, factors, the partition and schedule tables) and its Krylov
+ *    workspaces; ndiag_destroy releases them.
+ *  - Calls are ordered on the handle's CUDA stream. Calls that return values
+ *    to the host (krylov_solve, ndiag_residual_norm) synchronise that stream.
+ *    A device-side failure (a bounded wait that timed out) is reported at the
+ *    next synchronising call as NDIAG_ETIMEOUT.
+ *  - Not thread-safe per handle; distinct handles may be used concurrently.
+ *
+ * Matrix storage (Eq. d2d; Def. "structured n-diagonal matrix", Sec. 7): a
+ * structured n-diagonal matrix is given diagonal-major, s arrays of N values,
+ * entry k of row i being A(i, i + off_k) in the stencil order
+ *     5-point (2D): C W E S N
+ *     7-point (3D): C W E S N B F
+ *     9-point (2D): C W E S N SW SE NW NE
+ * Entries that point outside the grid must be 0 (Dirichlet values are folded
+ * into the right-hand side, Eq. 1d:mat).
+ */
+#ifndef NDIAG_H
+#define NDIAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ndiag ndiag;
+
+typedef enum {
+  NDIAG_OK = 0,
+  NDIAG_EINVAL = 1,     /* bad argument (size, pointer, enum, unsupported stencil) */
+  NDIAG_ENOMEM = 2,     /* device or host allocation failed */
+  NDIAG_ENOCONV = 3,    /* iteration limit reached before the tolerance */
+  NDIAG_EBREAKDOWN = 4, /* Krylov breakdown (rho = 0, (p,Ap) = 0, ...) or zero pivot */
+  NDIAG_EDEVICE = 5,    /* CUDA error; the message is in ndiag_last_error() */
+  NDIAG_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+  NDIAG_EBUSY = 7,      /* serving: request not finished yet */
+  NDIAG_ESTATE = 8      /* call out of order (e.g. ilu0_apply before ilu0_factor) */
+} ndiag_status;
+
+/* Precision of the sweeps and of the stored coefficients. */
+enum {
+  NDIAG_FP64 = 0,     /* fp64 vectors and coefficients */
+  NDIAG_FP32 = 1,     /* fp32 vectors and coefficients */
+  NDIAG_FP32_D16 = 2  /* fp32 vectors, coefficients stored as fp16 */
+};
+
+/* Ordering of a sweep. */
+enum {
+  NDIAG_NATURAL = 0,    /* lexicographic order over the whole grid */
+  NDIAG_DECOMPOSED = 1  /* the paper's decomposed multi-frontal order */
+};
+
+enum { NDIAG_PCG = 0, NDIAG_BICGSTAB = 1, NDIAG_STATIONARY = 2 };
+enum { NDIAG_PREC_NONE = 0, NDIAG_PREC_SSOR = 1, NDIAG_PREC_ILU0 = 2 };
+
+/* Optional device allocator (e.g. a framework's caching allocator). Without
+ * one the library calls cudaMallocAsync / cudaFreeAsync on its stream. */
+typedef void* (*ndiag_alloc_fn)(size_t bytes, void* cuda_stream, void* ctx);
+typedef void (*ndiag_free_fn)(void* ptr, size_t bytes, void* cuda_stream, void* ctx);
+ndiag_status ndiag_set_allocator(ndiag_alloc_fn alloc, ndiag_free_fn release, void* ctx);
+
+/* Text of the last error seen by this thread ("" if none). */
+const char* ndiag_last_error(void);
+
+/*
+ * ndiag_create -- copy a structured n-diagonal matrix to the device and build
+ * the partition and sweep schedule.
+ *   dim       2 or 3.
+ *   n         cells per axis, n[2] ignored when dim = 2; every n[a] >= 1.
+ *   stencil   5 (dim 2), 7 (dim 3) or 9 (dim 2).
+ *   diags     HOST array, stencil * N doubles, diagonal-major (see above);
+ *             read during the call only (the caller keeps ownership).
+ *   sub       subdomains per axis (Sec. 3 "Domain decomposition"): a Cartesian
+ *             split into nearly equal parts, the first n mod p parts one cell
+ *             longer; 1 <= sub[a] <= n[a].
+ *   precision NDIAG_FP64, NDIAG_FP32 or NDIAG_FP32_D16 (the precision of the
+ *             sweeps; residuals, dots and norms are always fp64).
+ *   cuda_stream  cudaStream_t (NULL = legacy default stream).
+ * Errors: NDIAG_EINVAL (sizes, stencil, diagonal <= 0), NDIAG_ENOMEM.
+ */
+ndiag_status ndiag_create(ndiag** out, int dim, const int64_t n[3], int stencil,
+                          const double* diags, const int sub[3], int precision,
+                          void* cuda_stream);
+
+void ndiag_destroy(ndiag* h);
+
+/* Number of cells N and the handle's precision. */
+int64_t ndiag_cells(const ndiag* h);
+int ndiag_precision(const ndiag* h);
+
+/*
+ * sor_sweep -- one SOR sweep u^(k) -> u^(k+1) at schedule phase t
+ * (Eqs. sor2d_sw..sor2d_nw; coupled start nodes by Eqs. 2d:sor4b4 and
+ * 2d:sor2b2; 3D by Sec. 4; the splitting form of Eq. ca2d:matiter):
+ *     (D + w L_J) u+ = ((1 - w) D - w U_J) u + w b,
+ * J = the implicit set of phase t, w = omega[start corner of the row's
+ * subdomain] (corner bit a set when the subdomain starts at its maximum
+ * coordinate along axis a; 2^dim entries, HOST array).
+ *   mode   NDIAG_DECOMPOSED (paper) or NDIAG_NATURAL (lexicographic).
+ *   b, x_old, x_new  DEVICE vectors of N values in the handle's precision
+ *          (double for FP64, float otherwise). x_new must not alias x_old:
+ *          a sweep reads old values of neighbouring subdomains (the halo of
+ *          Sec. 3 "Data structure") while they are being overwritten.
+ * Asynchronous on the handle's stream.
+ */
+ndiag_status sor_sweep(ndiag* h, int mode, const double* omega, int64_t t, const void* b,
+                       const void* x_old, void* x_new);
+
+/*
+ * ssor_apply -- symmetric SSOR preconditioner (Sec. 2: SSOR = a sweep and its
+ * reverse; Sec. 5), in the SPD form usable inside CG:
+ *     z = w (2 - w) (D + w L_J^T)^-1 D (D + w L_J)^-1 r,
+ * J = implicit set of the forward phase (the phase at which subdomain 0
+ * sweeps from the origin corner; with one subdomain this is classical SSOR).
+ *   r, z  DEVICE vectors (handle precision), z must not alias r.
+ */
+ndiag_status ssor_apply(ndiag* h, int mode, double omega, const void* r, void* z);
+
+/*
+ * ilu0_factor -- ILU(0) (Sec. 5: one symmetric Gauss-Seidel pass on an
+ * n-diagonal matrix is ILU(0)). DECOMPOSED: M = (D~ + L_J) D~^-1 (D~ + U_J),
+ * L_J / U_J = implicit entries of the forward phase / of its reverse, and
+ * d~_i = a_ii - sum_{j in J_i, i not in J_j} a_ij a_ji / d~_j. NATURAL: the
+ * same with one lexicographic subdomain (5/7-point).
+ * Errors: NDIAG_EBREAKDOWN on a zero pivot (reported at the next sync).
+ */
+ndiag_status ilu0_factor(ndiag* h, int mode);
+
+/* ilu0_apply -- z = M^-1 r: (D~ + L_J) y = r, then (D~ + U_J) z = D~ y.
+ * r, z DEVICE vectors (handle precision); z may alias r. ESTATE if not factored. */
+ndiag_status ilu0_apply(ndiag* h, const void* r, void* z);
+
+/* Residual r = b - A x in fp64 (A in fp64) and, if norm2 != NULL, ||r||_2
+ * copied to the host (synchronises). b, x, r: DEVICE double vectors. */
+ndiag_status ndiag_residual(ndiag* h, const double* b, const double* x, double* r, double* norm2);
+
+typedef struct {
+  int iterations;        /* Krylov iterations / sweeps / inner iterations in total */
+  int outer;             /* refinement steps (1 without refinement) */
+  double relres;         /* final TRUE fp64 ||b - A x|| / ||b|| */
+  double seconds;        /* wall time of the call */
+  int status;            /* same as the return value */
+} ndiag_solve_info;
+
+/*
+ * krylov_solve -- solve A x = b to ||b - A x||_2 / ||b||_2 <= rtol.
+ *   method  NDIAG_PCG, NDIAG_BICGSTAB or NDIAG_STATIONARY (SOR sweeps of the
+ *           schedule t = 0, 1, 2, ..., omega[] per direction).
+ *   precond NDIAG_PREC_NONE / SSOR / ILU0 (ignored for STATIONARY).
+ *   mode    NDIAG_DECOMPOSED or NDIAG_NATURAL ordering of the sweeps.
+ *   omega   HOST array of 2^dim relaxation factors (STATIONARY), omega[0] is
+ *           the SSOR factor.
+ *   b, x    fp64 vectors, DEVICE or HOST pointers (detected); x holds the
+ *           initial guess and receives the solution.
+ * Stop rule: the recurrence residual meets rtol, then the true fp64 residual is
+ * checked; if it is above rtol the method restarts from it. With precision
+ * FP32/FP32_D16 the solve is an fp64 iterative refinement around fp32 inner
+ * solves (inner tolerance 1e-5 relative).
+ * Errors: NDIAG_ENOCONV (maxit), NDIAG_EBREAKDOWN, NDIAG_ESTATE (ILU0 not factored).
+ */
+ndiag_status krylov_solve(ndiag* h, int method, int precond, int mode, const double* omega,
+                          double rtol, int maxit, const double* b, double* x,
+                          ndiag_solve_info* info);
+
+/*
+ * Counters of the library's own kernels on a handle, for measurement.
+ *  launches        kernels the library launched since the last ndiag_profile
+ *  sweep_launches  sweep kernels among them (one sweep = N cell updates; an
+ *                  ILU(0) or SSOR apply is two)
+ *  sweep_ms        summed device time of those sweep kernels, from CUDA events
+ *                  recorded on the handle's stream around each of them
+ *                  (only while profiling is enabled, else 0)
+ *  sweep_bytes     algorithmic bytes of those sweeps: every coefficient and
+ *                  vector value a sweep must read or write, once per cell
+ */
+typedef struct {
+  int64_t launches;
+  int64_t sweep_launches;
+  double sweep_ms;
+  double sweep_bytes;
+} ndiag_counters;
+
+/* Resets the counters; enable != 0 also times every sweep kernel. */
+ndiag_status ndiag_profile(ndiag* h, int enable);
+/* Synchronises the handle's stream and reports the counters. */
+ndiag_status ndiag_read_counters(ndiag* h, ndiag_counters* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NDIAG_H */

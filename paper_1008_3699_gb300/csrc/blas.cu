@@ -1,0 +1,388 @@
+// Vector kernels of the Krylov drivers: stencil SpMV, residual, fused
+// updates, and dot products with a deterministic two-level reduction (fixed
+// grid, fixed order; the last block to finish sums the block partials in
+// index order, so a result does not depend on scheduling).
+#include "blas.h"
+
+namespace nd {
+
+namespace {
+constexpr int BT = 256;  // threads per block
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < BT / 32; ++k) r += sh[k];
+  __syncthreads();
+  return r;  // valid in thread 0
+}
+
+// Writes NV block partials; the last block sums them into res[0..NV).
+template <int NV>
+__device__ void finish_reduce(const double (&v)[NV], Reduce R) {
+  __shared__ double sh[BT / 32];
+  __shared__ bool last;
+  double tot[NV];
+  for (int k = 0; k < NV; ++k) tot[k] = block_sum(v[k], sh);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NV; ++k) R.part[(size_t)k * gridDim.x + blockIdx.x] = tot[k];
+    __threadfence();
+    last = atomicAdd(R.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    for (int k = 0; k < NV; ++k) {
+      double acc = 0.0;
+      for (unsigned b = threadIdx.x; b < gridDim.x; b += BT) acc += __ldcg(R.part + (size_t)k * gridDim.x + b);
+      acc = block_sum(acc, sh);
+      if (threadIdx.x == 0) R.res[k] = acc;
+    }
+    if (threadIdx.x == 0) *R.counter = 0;
+  }
+}
+
+struct Geo {
+  int nx, ny, nz, stencil;
+  int64_t N;
+};
+
+// (A x)_i for a structured stencil; the matrix A is diagonal-major (s, N).
+template <class T, class TA>
+__device__ __forceinline__ T stencil_apply(const Geo& g, const TA* __restrict__ A, const T* __restrict__ x,
+                                           int64_t i) {
+  const int cx = (int)(i % g.nx);
+  const int64_t rest = i / g.nx;
+  const int cy = (int)(rest % g.ny);
+  const int cz = (int)(rest / g.ny);
+  const int64_t N = g.N;
+  T acc = (T)A[i] * x[i];
+  if (cx > 0) acc = fma((T)A[N + i], x[i - 1], acc);
+  if (cx + 1 < g.nx) acc = fma((T)A[2 * N + i], x[i + 1], acc);
+  if (cy > 0) acc = fma((T)A[3 * N + i], x[i - g.nx], acc);
+  if (cy + 1 < g.ny) acc = fma((T)A[4 * N + i], x[i + g.nx], acc);
+  if (g.stencil == 7) {
+    const int64_t pl = (int64_t)g.nx * g.ny;
+    if (cz > 0) acc = fma((T)A[5 * N + i], x[i - pl], acc);
+    if (cz + 1 < g.nz) acc = fma((T)A[6 * N + i], x[i + pl], acc);
+  } else if (g.stencil == 9) {
+    if (cx > 0 && cy > 0) acc = fma((T)A[5 * N + i], x[i - g.nx - 1], acc);
+    if (cx + 1 < g.nx && cy > 0) acc = fma((T)A[6 * N + i], x[i - g.nx + 1], acc);
+    if (cx > 0 && cy + 1 < g.ny) acc = fma((T)A[7 * N + i], x[i + g.nx - 1], acc);
+    if (cx + 1 < g.nx && cy + 1 < g.ny) acc = fma((T)A[8 * N + i], x[i + g.nx + 1], acc);
+  }
+  return acc;
+}
+
+// y = A x ; ND = 1: partial (w, y); ND = 2: also (y, y)
+template <class T, class TA, int ND>
+__global__ void __launch_bounds__(BT) spmv_kernel(Geo g, const TA* __restrict__ A, const T* __restrict__ x,
+                                                  T* __restrict__ y, const T* __restrict__ w, Reduce R) {
+  double d0 = 0.0, d1 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < g.N; i += (int64_t)gridDim.x * BT) {
+    const T v = stencil_apply<T, TA>(g, A, x, i);
+    y[i] = v;
+    if (ND >= 1) d0 += (double)w[i] * (double)v;
+    if (ND >= 2) d1 += (double)v * (double)v;
+  }
+  if (ND == 1) {
+    double vv[1] = {d0};
+    finish_reduce<1>(vv, R);
+  } else if (ND == 2) {
+    double vv[2] = {d0, d1};
+    finish_reduce<2>(vv, R);
+  }
+}
+
+// r = b - A x (fp64), ||r||^2
+template <class TB>
+__global__ void __launch_bounds__(BT) residual_kernel(Geo g, const double* __restrict__ A,
+                                                      const double* __restrict__ b, const double* __restrict__ x,
+                                                      TB* __restrict__ r, Reduce R) {
+  double d = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < g.N; i += (int64_t)gridDim.x * BT) {
+    const double v = b[i] - stencil_apply<double, double>(g, A, x, i);
+    r[i] = (TB)v;
+    d += v * v;
+  }
+  double vv[1] = {d};
+  finish_reduce<1>(vv, R);
+}
+
+// generic fused dots: up to 3 inner products (a_k, b_k)
+template <class T, int NV>
+__global__ void __launch_bounds__(BT) dots_kernel(int64_t N, const T* a0, const T* b0, const T* a1, const T* b1,
+                                                  const T* a2, const T* b2, Reduce R) {
+  double d[NV];
+  for (int k = 0; k < NV; ++k) d[k] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT) {
+    d[0] += (double)a0[i] * (double)b0[i];
+    if (NV > 1) d[1] += (double)a1[i] * (double)b1[i];
+    if (NV > 2) d[2] += (double)a2[i] * (double)b2[i];
+  }
+  finish_reduce<NV>(d, R);
+}
+
+// ---- BiCGSTAB steps (scalars live in device memory) ----
+// p = r + beta (p - om v),  beta = (rho/rho_old)(alpha/om)
+template <class T>
+__global__ void __launch_bounds__(BT) bicg_p_kernel(int64_t N, const T* r, T* p, const T* v, const double* sc,
+                                                    int first) {
+  const double rho = sc[SC_RHO], rho_old = sc[SC_RHO_OLD], alpha = sc[SC_ALPHA], om = sc[SC_OM];
+  const double beta = first ? 0.0 : (rho / rho_old) * (alpha / om);
+  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT) {
+    p[i] = first ? r[i] : (T)((double)r[i] + beta * ((double)p[i] - om * (double)v[i]));
+  }
+}
+// s = r - alpha v, alpha = rho / (rh, v); ||s||^2
+template <class T>
+__global__ void __launch_bounds__(BT) bicg_s_kernel(int64_t N, const T* r, const T* v, T* s, const double* sc,
+                                                    Reduce R) {
+  const double alpha = sc[SC_RHO] / sc[SC_RV];
+  double d = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT) {
+    const T sv = (T)((double)r[i] - alpha * (double)v[i]);
+    s[i] = sv;
+    d += (double)sv * (double)sv;
+  }
+  double vv[1] = {d};
+  finish_reduce<1>(vv, R);
+}
+// x += alpha ph + om sh ; r = s - om t ; ||r||^2, (rh, r)
+template <class T>
+__global__ void __launch_bounds__(BT) bicg_xr_kernel(int64_t N, T* x, const T* ph, const T* sh, T* r, const T* s,
+                                                     const T* t, const T* rh, const double* sc, Reduce R) {
+  const double alpha = sc[SC_RHO] / sc[SC_RV];
+  const double tt = sc[SC_TT];
+  const double om = tt == 0.0 ? 0.0 : sc[SC_TS] / tt;
+  double d0 = 0.0, d1 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT) {
+    x[i] = (T)((double)x[i] + alpha * (double)ph[i] + om * (double)sh[i]);
+    const T rv = (T)((double)s[i] - om * (double)t[i]);
+    r[i] = rv;
+    d0 += (double)rv * (double)rv;
+    d1 += (double)rh[i] * (double)rv;
+  }
+  double vv[2] = {d0, d1};
+  finish_reduce<2>(vv, R);
+}
+// x += alpha ph  (exit at the half step)
+template <class T>
+__global__ void __launch_bounds__(BT) axpy_alpha_kernel(int64_t N, T* x, const T* ph, const double* sc) {
+  const double alpha = sc[SC_RHO] / sc[SC_RV];
+  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT)
+    x[i] = (T)((double)x[i] + alpha * (double)ph[i]);
+}
+
+// ---- PCG steps ----
+// x += alpha p ; r -= alpha q ; ||r||^2 ; alpha = rz / (p, q)
+template <class T>
+__global__ void __launch_bounds__(BT) cg_xr_kernel(int64_t N, T* x, const T* p, T* r, const T* q, const double* sc,
+                                                   Reduce R) {
+  const double alpha = sc[SC_RZ] / sc[SC_PQ];
+  double d = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT) {
+    x[i] = (T)((double)x[i] + alpha * (double)p[i]);
+    const T rv = (T)((double)r[i] - alpha * (double)q[i]);
+    r[i] = rv;
+    d += (double)rv * (double)rv;
+  }
+  double vv[1] = {d};
+  finish_reduce<1>(vv, R);
+}
+// p = z + beta p, beta = rz_new / rz ; first: p = z
+template <class T>
+__global__ void __launch_bounds__(BT) cg_p_kernel(int64_t N, const T* z, T* p, const double* sc, int first) {
+  const double beta = first ? 0.0 : sc[SC_RZ_NEW] / sc[SC_RZ];
+  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT)
+    p[i] = first ? z[i] : (T)((double)z[i] + beta * (double)p[i]);
+}
+
+__global__ void copy_scalar_kernel(double* sc, int dst, int src) { sc[dst] = sc[src]; }
+
+template <class TD, class TS>
+__global__ void __launch_bounds__(BT) convert_kernel(int64_t N, const TS* s, TD* d) {
+  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT) d[i] = (TD)s[i];
+}
+__global__ void __launch_bounds__(BT) add_to_kernel(int64_t N, double* x, const float* e) {
+  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT) x[i] += (double)e[i];
+}
+template <class T>
+__global__ void __launch_bounds__(BT) scale_kernel(int64_t N, T* x, double f) {
+  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT)
+    x[i] = (T)((double)x[i] * f);
+}
+template <class T>
+__global__ void __launch_bounds__(BT) mul_kernel(int64_t N, const double* A0, const T* x, T* y) {
+  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT)
+    y[i] = (T)(A0[i] * (double)x[i]);
+}
+
+Geo geo(const Handle* h) {
+  return Geo{(int)h->n[0], (int)h->n[1], (int)h->n[2], h->stencil, h->N};
+}
+}  // namespace
+
+int grid_blocks(const Handle* h) {
+  const int64_t need = (h->N + BT - 1) / BT;
+  const int64_t cap = (int64_t)h->sm_count * 8;
+  return (int)(need < cap ? (need < 1 ? 1 : need) : cap);
+}
+
+Reduce reduce_slot(Handle* h, int slot) {
+  Reduce R;
+  const int G = grid_blocks(h);
+  R.part = h->red + RED_RES + (size_t)slot * 4 * G;  // 4 values per slot region
+  R.counter = (unsigned*)(h->red) + 2 * slot;
+  R.res = h->red + SC_BASE;  // overridden by callers
+  return R;
+}
+
+size_t reduce_bytes(const Handle* h) {
+  return sizeof(double) * (RED_RES + (size_t)RED_SLOTS * 4 * grid_blocks(h));
+}
+
+#define LAUNCH(kern, ...) \
+  do {                                                          \
+    ++h->launches;                                              \
+    kern<<<grid_blocks(h), BT, 0, h->stream>>>(__VA_ARGS__);    \
+    ND_CUDA(cudaGetLastError());                                \
+  } while (0)
+
+ndiag_status spmv64(Handle* h, const double* x, double* y) {
+  Reduce R{};
+  LAUNCH((spmv_kernel<double, double, 0>), geo(h), h->A64, x, y, (const double*)nullptr, R);
+  return NDIAG_OK;
+}
+
+template <class T>
+ndiag_status spmv_dot(Handle* h, const T* x, T* y, const T* w, double* res, int slot, bool two) {
+  Reduce R = reduce_slot(h, slot);
+  R.res = res;
+  if (sizeof(T) == 8) {
+    if (two) LAUNCH((spmv_kernel<T, double, 2>), geo(h), h->A64, x, y, w, R);
+    else LAUNCH((spmv_kernel<T, double, 1>), geo(h), h->A64, x, y, w, R);
+  } else {
+    if (two) LAUNCH((spmv_kernel<T, float, 2>), geo(h), (const float*)h->Alo, x, y, w, R);
+    else LAUNCH((spmv_kernel<T, float, 1>), geo(h), (const float*)h->Alo, x, y, w, R);
+  }
+  return NDIAG_OK;
+}
+template <class T>
+ndiag_status spmv_any(Handle* h, const T* x, T* y) {
+  Reduce R{};
+  if (sizeof(T) == 8)
+    LAUNCH((spmv_kernel<T, double, 0>), geo(h), h->A64, x, y, (const T*)nullptr, R);
+  else
+    LAUNCH((spmv_kernel<T, float, 0>), geo(h), (const float*)h->Alo, x, y, (const T*)nullptr, R);
+  return NDIAG_OK;
+}
+
+ndiag_status residual64(Handle* h, const double* b, const double* x, double* r, double* res) {
+  Reduce R = reduce_slot(h, 0);
+  R.res = res;
+  LAUNCH((residual_kernel<double>), geo(h), h->A64, b, x, r, R);
+  return NDIAG_OK;
+}
+ndiag_status residual64_to32(Handle* h, const double* b, const double* x, float* r, double* res) {
+  Reduce R = reduce_slot(h, 0);
+  R.res = res;
+  LAUNCH((residual_kernel<float>), geo(h), h->A64, b, x, r, R);
+  return NDIAG_OK;
+}
+
+template <class T>
+ndiag_status dots(Handle* h, int nv, const T* a0, const T* b0, const T* a1, const T* b1, const T* a2,
+                  const T* b2, double* res, int slot) {
+  Reduce R = reduce_slot(h, slot);
+  R.res = res;
+  if (nv == 1) LAUNCH((dots_kernel<T, 1>), h->N, a0, b0, a1, b1, a2, b2, R);
+  else if (nv == 2) LAUNCH((dots_kernel<T, 2>), h->N, a0, b0, a1, b1, a2, b2, R);
+  else LAUNCH((dots_kernel<T, 3>), h->N, a0, b0, a1, b1, a2, b2, R);
+  return NDIAG_OK;
+}
+
+template <class T>
+ndiag_status bicg_p(Handle* h, const T* r, T* p, const T* v, const double* sc, int first) {
+  LAUNCH((bicg_p_kernel<T>), h->N, r, p, v, sc, first);
+  return NDIAG_OK;
+}
+template <class T>
+ndiag_status bicg_s(Handle* h, const T* r, const T* v, T* s, double* sc) {
+  Reduce R = reduce_slot(h, 1);
+  R.res = sc + SC_SS;
+  LAUNCH((bicg_s_kernel<T>), h->N, r, v, s, sc, R);
+  return NDIAG_OK;
+}
+template <class T>
+ndiag_status bicg_xr(Handle* h, T* x, const T* ph, const T* sh, T* r, const T* s, const T* t, const T* rh,
+                     double* sc) {
+  Reduce R = reduce_slot(h, 2);
+  R.res = sc + SC_RR;  // writes SC_RR, SC_RR+1 (= SC_RHO_NEXT)
+  LAUNCH((bicg_xr_kernel<T>), h->N, x, ph, sh, r, s, t, rh, sc, R);
+  return NDIAG_OK;
+}
+template <class T>
+ndiag_status axpy_alpha(Handle* h, T* x, const T* ph, const double* sc) {
+  LAUNCH((axpy_alpha_kernel<T>), h->N, x, ph, sc);
+  return NDIAG_OK;
+}
+template <class T>
+ndiag_status cg_xr(Handle* h, T* x, const T* p, T* r, const T* q, double* sc) {
+  Reduce R = reduce_slot(h, 1);
+  R.res = sc + SC_RR;
+  LAUNCH((cg_xr_kernel<T>), h->N, x, p, r, q, sc, R);
+  return NDIAG_OK;
+}
+template <class T>
+ndiag_status cg_p(Handle* h, const T* z, T* p, const double* sc, int first) {
+  LAUNCH((cg_p_kernel<T>), h->N, z, p, sc, first);
+  return NDIAG_OK;
+}
+ndiag_status copy_scalar(Handle* h, double* sc, int dst, int src) {
+  ++h->launches;
+  copy_scalar_kernel<<<1, 1, 0, h->stream>>>(sc, dst, src);
+  ND_CUDA(cudaGetLastError());
+  return NDIAG_OK;
+}
+ndiag_status to32(Handle* h, const double* s, float* d) {
+  LAUNCH((convert_kernel<float, double>), h->N, s, d);
+  return NDIAG_OK;
+}
+ndiag_status add_to(Handle* h, double* x, const float* e) {
+  LAUNCH(add_to_kernel, h->N, x, e);
+  return NDIAG_OK;
+}
+template <class T>
+ndiag_status scale(Handle* h, T* x, double f) {
+  LAUNCH((scale_kernel<T>), h->N, x, f);
+  return NDIAG_OK;
+}
+template <class T>
+ndiag_status mul_diag(Handle* h, const T* x, T* y) {
+  LAUNCH((mul_kernel<T>), h->N, h->A64, x, y);
+  return NDIAG_OK;
+}
+
+#define INST(T)                                                                                         \
+  template ndiag_status spmv_dot<T>(Handle*, const T*, T*, const T*, double*, int, bool);                    \
+  template ndiag_status spmv_any<T>(Handle*, const T*, T*);                                            \
+  template ndiag_status dots<T>(Handle*, int, const T*, const T*, const T*, const T*, const T*,         \
+                                const T*, double*, int);                                               \
+  template ndiag_status bicg_p<T>(Handle*, const T*, T*, const T*, const double*, int);                \
+  template ndiag_status bicg_s<T>(Handle*, const T*, const T*, T*, double*);                           \
+  template ndiag_status bicg_xr<T>(Handle*, T*, const T*, const T*, T*, const T*, const T*, const T*,  \
+                                   double*);                                                           \
+  template ndiag_status axpy_alpha<T>(Handle*, T*, const T*, const double*);                           \
+  template ndiag_status cg_xr<T>(Handle*, T*, const T*, T*, const T*, double*);                        \
+  template ndiag_status cg_p<T>(Handle*, const T*, T*, const double*, int);                            \
+  template ndiag_status scale<T>(Handle*, T*, double);                                                 \
+  template ndiag_status mul_diag<T>(Handle*, const T*, T*);
+INST(double)
+INST(float)
+
+}  // namespace nd

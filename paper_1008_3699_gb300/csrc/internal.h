@@ -1,0 +1,152 @@
+// Internal declarations of the GB300 sweep library (not part of the C ABI).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ndiag.h"
+
+namespace nd {
+
+// ---------------------------------------------------------------------------
+// Errors and allocation
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+ndiag_status cuda_status(cudaError_t e, const char* what);
+#define ND_CUDA(call)                                              \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return ::nd::cuda_status(e_, #call);    \
+  } while (0)
+#define ND_TRY(call)                              \
+  do {                                            \
+    ndiag_status s_ = (call);                     \
+    if (s_ != NDIAG_OK) return s_;                \
+  } while (0)
+
+void* dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void* p, size_t bytes, cudaStream_t s);
+
+// Stencil entries (diagonal-major storage order of the C ABI).
+enum { EC = 0, EW = 1, EE = 2, ES = 3, EN = 4, EB = 5, EF = 6,
+       ESW = 5, ESE = 6, ENW = 7, ENE = 8 };
+
+// Internal ordering value: the natural ordering run backwards (the backward
+// halves of ILU(0) and SSOR in natural mode).
+enum { MODE_NATURAL_REV = 2 };
+
+// Sweep kinds (what one cell update computes; see sweep2d.cu).
+enum SweepKind {
+  KIND_SOR = 0,         // x = (1-w) u + w (inv*b - sum_old c u) - w sum_J c x
+  KIND_TRI_SCALED = 1,  // x = inv*r - w sum_J c x     (ILU forward, SSOR forward)
+  KIND_TRI_UNIT = 2     // x = r - w sum_J c x         (ILU backward)
+};
+
+// Scaled coefficient set: inv[i] = 1/pivot_i, c[e][i] = A(i, e) / pivot_i for
+// every off-diagonal entry e (pivot = a_ii for SOR/SSOR, d~_i for ILU(0)).
+struct ScaledSet {
+  void* base = nullptr;  // one allocation: s arrays of N values (inv, then entries 1..s-1)
+  size_t bytes = 0;
+};
+
+// Device-side status words (error flag written by bounded waits).
+struct DevStatus {
+  int timeout;      // a bounded wait gave up
+  int zero_pivot;   // ILU factor met a zero pivot
+};
+
+struct Workspace {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct ProfRec {
+  cudaEvent_t a = nullptr, b = nullptr;
+  double bytes = 0.0;
+};
+
+struct Handle {
+  int dim = 0, stencil = 0, precision = 0;
+  int64_t n[3] = {1, 1, 1};
+  int64_t N = 0;
+  int sub[3] = {1, 1, 1};
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  size_t vec_bytes = 0;   // bytes of one vector in the handle's precision
+
+  double* A64 = nullptr;  // s * N raw matrix, fp64 (residuals, SpMV)
+  void* Alo = nullptr;    // s * N raw matrix in the sweep precision (fp32 inner SpMV)
+  ScaledSet sor;          // pivots a_ii
+  ScaledSet ilu;          // pivots d~_i
+  ScaledSet sorT;         // transposed entries A(j, i) / a_ii (SSOR backward solve)
+  unsigned* vcount = nullptr;    // per subdomain vertex: edges finished (self-resetting)
+  size_t vcount_bytes = 0;
+  int ilu_mode = -1;
+
+  // sweep scratch: progress flags / ticket / twin handoff for multi-CTA subdomains
+  unsigned* sync = nullptr;
+  size_t sync_bytes = 0;
+  void* twin_hand = nullptr;
+  size_t twin_hand_bytes = 0;
+  DevStatus* status = nullptr;   // device
+
+  // Krylov workspace (allocated on first use)
+  Workspace kws;
+  double* red = nullptr;         // reduction partials + results (device)
+  size_t red_bytes = 0;
+  double* red_host = nullptr;    // pinned mirror of the results
+  void* tmp = nullptr;           // one vector in sweep precision (ssor/ilu intermediates)
+  size_t tmp_bytes = 0;
+
+  // counters (ndiag_profile / ndiag_read_counters)
+  int64_t launches = 0;
+  int64_t sweep_launches = 0;
+  double sweep_ms = 0.0;
+  double sweep_bytes = 0.0;
+  bool profiling = false;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> ev_pool;
+};
+
+// Sweep-launch timing: brackets a sweep kernel with events when profiling is
+// on and records its algorithmic bytes.
+int prof_begin(Handle* h);
+void prof_end(Handle* h, int slot, double bytes);
+
+// Partition of n cells into p parts, the first n mod p parts one longer.
+struct Split {
+  int p, q, r;
+  __host__ __device__ int lo(int k) const { return k * q + (k < r ? k : r); }
+  __host__ __device__ int len(int k) const { return q + (k < r ? 1 : 0); }
+};
+
+// Start corner of subdomain 0 at phase t (Sec. 2 step (ii); Sec. 3 "Sweeping
+// directions"; Sec. 4): 1D alternates starting left-to-right; in 2D/3D the
+// corner is the all-ones corner with floor((t mod 2^d)/2) flipped on x, y, and
+// reversed on odd t.
+int base_corner(int dim, int64_t t);
+// Forward phase of the preconditioners: subdomain 0 sweeps from its origin.
+inline int64_t fwd_phase(int dim) { return dim == 1 ? 0 : 1; }
+
+// Launchers (sweep2d.cu)
+ndiag_status launch_sweep2d(Handle* h, int kind, int mode, int64_t t, const double* omega,
+                            const ScaledSet& set, const void* rhs, const void* xold, void* xnew);
+ndiag_status launch_sweep2d_ex(Handle* h, int kind, int mode, int64_t t, const double* omega,
+                               const ScaledSet& set, const void* rhs, const void* xold, void* xnew,
+                               double beta_scale, bool reverse_interior);
+ndiag_status launch_ssor_edges2d(Handle* h, int mode, double omega, const void* w, void* z);
+ndiag_status build_scaled(Handle* h, ScaledSet& set, const double* piv);
+ndiag_status build_scaled_transposed(Handle* h, ScaledSet& set);
+
+// BLAS-1 and SpMV (blas.cu)
+ndiag_status spmv64(Handle* h, const double* x, double* y);
+ndiag_status residual64(Handle* h, const double* b, const double* x, double* r, double* norm2_dev);
+int reduce_blocks(const Handle* h);
+
+}  // namespace nd
+
+struct ndiag : nd::Handle {};

@@ -1,0 +1,393 @@
+// Krylov drivers: PCG, right-preconditioned BiCGSTAB, the stationary SOR
+// iteration, and fp64 iterative refinement around fp32 inner solves. Scalars
+// stay on the device; the host reads the residual norms once or twice per
+// iteration to decide convergence.
+#include <chrono>
+#include <cmath>
+
+#include "blas.h"
+#include "internal.h"
+
+namespace nd {
+
+ndiag_status do_ilu_apply(Handle* h, const void* r, void* z);
+ndiag_status do_ssor_apply(Handle* h, int mode, double omega, const void* r, void* z);
+ndiag_status check_device_status(Handle* h);
+
+namespace {
+
+__global__ void bicg_scalars_kernel(double* sc, int first) {
+  if (first) {
+    sc[SC_RHO_OLD] = 1.0;
+    sc[SC_ALPHA] = 1.0;
+    sc[SC_OM] = 1.0;
+  } else {
+    sc[SC_RHO_OLD] = sc[SC_RHO];
+    sc[SC_ALPHA] = sc[SC_RHO] / sc[SC_RV];
+    sc[SC_OM] = sc[SC_TT] == 0.0 ? 0.0 : sc[SC_TS] / sc[SC_TT];
+  }
+  sc[SC_RHO] = sc[SC_RHO_NEXT];
+}
+
+template <class T>
+__global__ void copy_kernel(int64_t N, const T* s, T* d) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = s[i];
+}
+template <class T>
+__global__ void zero_kernel(int64_t N, T* d) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = T(0);
+}
+
+template <class T>
+ndiag_status vcopy(Handle* h, const T* s, T* d) {
+  ++h->launches;
+  copy_kernel<T><<<h->sm_count * 4, 256, 0, h->stream>>>(h->N, s, d);
+  ND_CUDA(cudaGetLastError());
+  return NDIAG_OK;
+}
+template <class T>
+ndiag_status vzero(Handle* h, T* d) {
+  ++h->launches;
+  zero_kernel<T><<<h->sm_count * 4, 256, 0, h->stream>>>(h->N, d);
+  ND_CUDA(cudaGetLastError());
+  return NDIAG_OK;
+}
+
+// Reads the device scalars [SC_BASE, SC_END) into the pinned mirror.
+ndiag_status pull(Handle* h) {
+  ND_CUDA(cudaMemcpyAsync(h->red_host + SC_BASE, h->red + SC_BASE, sizeof(double) * (SC_END - SC_BASE),
+                          cudaMemcpyDeviceToHost, h->stream));
+  ND_CUDA(cudaStreamSynchronize(h->stream));
+  return NDIAG_OK;
+}
+
+struct Prec {
+  int kind;
+  int mode;
+  double omega;
+};
+
+ndiag_status apply_prec(Handle* h, const Prec& P, const void* r, void* z, size_t bytes) {
+  if (P.kind == NDIAG_PREC_ILU0) return do_ilu_apply(h, r, z);
+  if (P.kind == NDIAG_PREC_SSOR) return do_ssor_apply(h, P.mode, P.omega, r, z);
+  ND_CUDA(cudaMemcpyAsync(z, r, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  return NDIAG_OK;
+}
+
+template <class T>
+struct KV {
+  T *r, *rh, *p, *v, *ph, *s, *sh, *t;
+};
+
+// Initial residual r = b - A x for the vector type T. fp64: exact residual
+// kernel. fp32 inner solves start from x = 0, so r = b.
+template <class T>
+ndiag_status init_residual(Handle* h, const T* b, const T* x, T* r, double* rr_dev, bool x_is_zero) {
+  if (sizeof(T) == 8) return residual64(h, (const double*)b, (const double*)x, (double*)r, rr_dev);
+  if (!x_is_zero) {
+    set_error("fp32 inner solve must start from zero");
+    return NDIAG_EINVAL;
+  }
+  ND_TRY(vcopy<T>(h, b, r));
+  return dots<T>(h, 1, r, r, nullptr, nullptr, nullptr, nullptr, rr_dev, 3);
+}
+
+// BiCGSTAB (van der Vorst 1992), right preconditioned. Stops when the
+// recurrence residual meets tol_abs; with `recheck`, then verifies the true
+// residual and restarts from it if it is above tol_abs.
+template <class T>
+ndiag_status bicgstab(Handle* h, const Prec& P, const T* b, T* x, const KV<T>& V, double tol_abs, int maxit,
+                      bool recheck, bool x_is_zero, int* iters) {
+  double* sc = h->red;
+  const double* hs = h->red_host;
+  const size_t vb = sizeof(T) * (size_t)h->N;
+  int it = 0;
+  for (;;) {
+    ND_TRY(init_residual<T>(h, b, x, V.r, sc + SC_R0, x_is_zero));
+    ND_TRY(pull(h));
+    if (std::sqrt(hs[SC_R0]) <= tol_abs) break;
+    ND_TRY(vcopy<T>(h, V.r, V.rh));
+    ND_TRY(dots<T>(h, 1, V.rh, V.r, nullptr, nullptr, nullptr, nullptr, sc + SC_RHO_NEXT, 1));
+    bool converged = false;
+    int first = 1;
+    while (it < maxit) {
+      ++h->launches;
+      bicg_scalars_kernel<<<1, 1, 0, h->stream>>>(sc, first);
+      ND_CUDA(cudaGetLastError());
+      ND_TRY(bicg_p<T>(h, V.r, V.p, V.v, sc, first));
+      first = 0;
+      ND_TRY(apply_prec(h, P, V.p, V.ph, vb));
+      ND_TRY(spmv_dot<T>(h, V.ph, V.v, V.rh, sc + SC_RV, 1));
+      ND_TRY(bicg_s<T>(h, V.r, V.v, V.s, sc));
+      ND_TRY(pull(h));
+      if (hs[SC_RHO] == 0.0 || hs[SC_RV] == 0.0 || !std::isfinite(hs[SC_SS])) {
+        *iters = it;
+        set_error("BiCGSTAB breakdown");
+        return NDIAG_EBREAKDOWN;
+      }
+      ++it;
+      if (std::sqrt(hs[SC_SS]) <= tol_abs) {
+        ND_TRY(axpy_alpha<T>(h, x, V.ph, sc));
+        converged = true;
+        break;
+      }
+      ND_TRY(apply_prec(h, P, V.s, V.sh, vb));
+      ND_TRY(spmv_dot<T>(h, V.sh, V.t, V.s, sc + SC_TS, 2, true));
+      ND_TRY(bicg_xr<T>(h, x, V.ph, V.sh, V.r, V.s, V.t, V.rh, sc));
+      ND_TRY(pull(h));
+      if (!std::isfinite(hs[SC_RR])) {
+        *iters = it;
+        set_error("BiCGSTAB breakdown (non-finite residual)");
+        return NDIAG_EBREAKDOWN;
+      }
+      if (std::sqrt(hs[SC_RR]) <= tol_abs) {
+        converged = true;
+        break;
+      }
+      if (hs[SC_TT] == 0.0 || hs[SC_TS] == 0.0) {
+        *iters = it;
+        set_error("BiCGSTAB breakdown (omega = 0)");
+        return NDIAG_EBREAKDOWN;
+      }
+    }
+    if (!converged) {
+      *iters = it;
+      return NDIAG_ENOCONV;
+    }
+    if (!recheck) break;
+    x_is_zero = false;
+  }
+  *iters = it;
+  return NDIAG_OK;
+}
+
+// Preconditioned CG (Saad Alg. 9.1), same stop rule.
+template <class T>
+ndiag_status pcg(Handle* h, const Prec& P, const T* b, T* x, const KV<T>& V, double tol_abs, int maxit,
+                 bool recheck, bool x_is_zero, int* iters) {
+  double* sc = h->red;
+  const double* hs = h->red_host;
+  const size_t vb = sizeof(T) * (size_t)h->N;
+  T *r = V.r, *z = V.s, *p = V.p, *q = V.v;
+  int it = 0;
+  for (;;) {
+    ND_TRY(init_residual<T>(h, b, x, r, sc + SC_R0, x_is_zero));
+    ND_TRY(pull(h));
+    if (std::sqrt(hs[SC_R0]) <= tol_abs) break;
+    ND_TRY(apply_prec(h, P, r, z, vb));
+    ND_TRY(dots<T>(h, 1, r, z, nullptr, nullptr, nullptr, nullptr, sc + SC_RZ, 1));
+    ND_TRY(cg_p<T>(h, z, p, sc, 1));
+    bool converged = false;
+    while (it < maxit) {
+      ND_TRY(spmv_dot<T>(h, p, q, p, sc + SC_PQ, 2));
+      ND_TRY(cg_xr<T>(h, x, p, r, q, sc));
+      ND_TRY(pull(h));
+      if (hs[SC_PQ] == 0.0 || hs[SC_RZ] == 0.0 || !std::isfinite(hs[SC_RR])) {
+        *iters = it;
+        set_error("PCG breakdown");
+        return NDIAG_EBREAKDOWN;
+      }
+      ++it;
+      if (std::sqrt(hs[SC_RR]) <= tol_abs) {
+        converged = true;
+        break;
+      }
+      ND_TRY(apply_prec(h, P, r, z, vb));
+      ND_TRY(dots<T>(h, 1, r, z, nullptr, nullptr, nullptr, nullptr, sc + SC_RZ_NEW, 1));
+      ND_TRY(cg_p<T>(h, z, p, sc, 0));
+      ND_TRY(copy_scalar(h, sc, SC_RZ, SC_RZ_NEW));
+    }
+    if (!converged) {
+      *iters = it;
+      return NDIAG_ENOCONV;
+    }
+    if (!recheck) break;
+    x_is_zero = false;
+  }
+  *iters = it;
+  return NDIAG_OK;
+}
+
+// Stationary SOR iteration with the schedule t = 0, 1, 2, ...: stops at the
+// first iterate whose true residual meets tol_abs (checked after every sweep).
+template <class T>
+ndiag_status stationary(Handle* h, int mode, const double* omega, const T* b, T* x, T* xalt, T* r,
+                        double tol_abs, int maxit, bool x_is_zero, int* iters) {
+  double* sc = h->red;
+  const double* hs = h->red_host;
+  ND_TRY(init_residual<T>(h, b, x, r, sc + SC_R0, x_is_zero));
+  ND_TRY(pull(h));
+  double rel = std::sqrt(hs[SC_R0]);
+  int it = 0;
+  T* cur = x;
+  T* nxt = xalt;
+  while (rel > tol_abs && it < maxit) {
+    ND_TRY(launch_sweep2d(h, KIND_SOR, mode, it, omega, h->sor, b, cur, nxt));
+    ++it;
+    if (sizeof(T) == 8) {
+      ND_TRY(residual64(h, (const double*)b, (const double*)nxt, (double*)r, sc + SC_R0));
+    } else {
+      ND_TRY(spmv_any<T>(h, nxt, r));
+      // r = b - A x in fp32 with the norm in fp64 (inner solve only)
+      ND_TRY(dots<T>(h, 1, r, r, nullptr, nullptr, nullptr, nullptr, sc + SC_R0, 3));
+      set_error("fp32 stationary inner residual not supported");
+      return NDIAG_EINVAL;
+    }
+    ND_TRY(pull(h));
+    rel = std::sqrt(hs[SC_R0]);
+    T* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  if (cur != x) ND_TRY(vcopy<T>(h, cur, x));
+  *iters = it;
+  return rel <= tol_abs ? NDIAG_OK : NDIAG_ENOCONV;
+}
+
+ndiag_status ensure_kws(Handle* h, size_t bytes) {
+  if (h->kws.bytes >= bytes) return NDIAG_OK;
+  dev_free(h->kws.p, h->kws.bytes, h->stream);
+  h->kws.p = dev_alloc(bytes, h->stream);
+  h->kws.bytes = h->kws.p ? bytes : 0;
+  return h->kws.p ? NDIAG_OK : NDIAG_ENOMEM;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+KV<T> carve(char*& cur, int64_t N) {
+  KV<T> V;
+  T** slots[8] = {&V.r, &V.rh, &V.p, &V.v, &V.ph, &V.s, &V.sh, &V.t};
+  for (T** s : slots) {
+    *s = (T*)cur;
+    cur += ((sizeof(T) * (size_t)N + 255) / 256) * 256;
+  }
+  return V;
+}
+
+}  // namespace
+}  // namespace nd
+
+using namespace nd;
+
+extern "C" ndiag_status krylov_solve(ndiag* h, int method, int precond, int mode, const double* omega,
+                                     double rtol, int maxit, const double* b, double* x,
+                                     ndiag_solve_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!h || !b || !x || !omega || !(rtol > 0.0) || maxit < 0) return NDIAG_EINVAL;
+  if (method < NDIAG_PCG || method > NDIAG_STATIONARY) return NDIAG_EINVAL;
+  if (precond < NDIAG_PREC_NONE || precond > NDIAG_PREC_ILU0) return NDIAG_EINVAL;
+  if (mode != NDIAG_NATURAL && mode != NDIAG_DECOMPOSED) return NDIAG_EINVAL;
+  if (method != NDIAG_STATIONARY && precond == NDIAG_PREC_ILU0 && h->ilu_mode < 0) {
+    set_error("ILU(0) preconditioner requested before ilu0_factor");
+    return NDIAG_ESTATE;
+  }
+  const int64_t N = h->N;
+  const size_t v64 = ((sizeof(double) * (size_t)N + 255) / 256) * 256;
+  const size_t v32 = ((sizeof(float) * (size_t)N + 255) / 256) * 256;
+  const bool fp64 = h->precision == NDIAG_FP64;
+  const bool dev_b = is_device_ptr(b), dev_x = is_device_ptr(x);
+  // fp64 vectors: 8 Krylov + alt + b copy + x copy ; fp32: 8 inner + e + r64 + b + x
+  const size_t need = fp64 ? v64 * 11 : v32 * 9 + v64 * 3;
+  ND_TRY(ensure_kws(h, need));
+  char* cur = (char*)h->kws.p;
+  Prec P{precond, mode, omega[0]};
+  int iters = 0, outer = 0;
+  ndiag_status st = NDIAG_OK;
+  double bnorm = 0.0, relres = 0.0;
+  if (fp64) {
+    KV<double> V = carve<double>(cur, N);
+    double* xalt = (double*)cur;
+    cur += v64;
+    double* bd = dev_b ? (double*)b : (double*)cur;
+    cur += v64;
+    double* xd = dev_x ? x : (double*)cur;
+    if (!dev_b) ND_CUDA(cudaMemcpyAsync(bd, b, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+    if (!dev_x) ND_CUDA(cudaMemcpyAsync(xd, x, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+    ND_TRY(dots<double>(h, 1, bd, bd, nullptr, nullptr, nullptr, nullptr, h->red + SC_BB, 3));
+    ND_TRY(pull(h));
+    bnorm = std::sqrt(h->red_host[SC_BB]);
+    const double tol = rtol * (bnorm > 0 ? bnorm : 1.0);
+    if (method == NDIAG_BICGSTAB) st = bicgstab<double>(h, P, bd, xd, V, tol, maxit, true, false, &iters);
+    else if (method == NDIAG_PCG) st = pcg<double>(h, P, bd, xd, V, tol, maxit, true, false, &iters);
+    else st = stationary<double>(h, mode, omega, bd, xd, xalt, V.r, tol, maxit, false, &iters);
+    outer = 1;
+    if (st == NDIAG_OK || st == NDIAG_ENOCONV) {
+      ndiag_status s2 = residual64(h, bd, xd, V.r, h->red + SC_R0);
+      if (s2 == NDIAG_OK) s2 = pull(h);
+      if (s2 != NDIAG_OK) st = s2;
+      relres = std::sqrt(h->red_host[SC_R0]) / (bnorm > 0 ? bnorm : 1.0);
+    }
+    if (!dev_x) ND_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+  } else {
+    KV<float> V = carve<float>(cur, N);
+    float* e = (float*)cur;
+    cur += v32;
+    double* r64 = (double*)cur;
+    cur += v64;
+    double* bd = dev_b ? (double*)b : (double*)cur;
+    cur += v64;
+    double* xd = dev_x ? x : (double*)cur;
+    if (!dev_b) ND_CUDA(cudaMemcpyAsync(bd, b, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+    if (!dev_x) ND_CUDA(cudaMemcpyAsync(xd, x, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+    ND_TRY(dots<double>(h, 1, bd, bd, nullptr, nullptr, nullptr, nullptr, h->red + SC_BB, 3));
+    ND_TRY(pull(h));
+    bnorm = std::sqrt(h->red_host[SC_BB]);
+    const double tol = rtol * (bnorm > 0 ? bnorm : 1.0);
+    const double inner_rtol = 1e-5;
+    int max_outer = 60;
+    for (;;) {
+      // fp64 residual of the outer iterate, delivered in fp32 to the inner solve
+      ND_TRY(residual64_to32(h, bd, xd, V.t, h->red + SC_R0));
+      ND_TRY(pull(h));
+      const double rn = std::sqrt(h->red_host[SC_R0]);
+      relres = rn / (bnorm > 0 ? bnorm : 1.0);
+      if (rn <= tol) break;
+      if (outer >= max_outer || iters >= maxit) {
+        st = NDIAG_ENOCONV;
+        break;
+      }
+      ++outer;
+      ND_TRY(vzero<float>(h, e));
+      int it_in = 0;
+      // the inner solve's right-hand side lives in V.t; copy it out first
+      ND_TRY(vcopy<float>(h, V.t, (float*)r64));
+      const double tol_in = inner_rtol * rn;
+      ndiag_status si;
+      if (method == NDIAG_PCG) si = pcg<float>(h, P, (float*)r64, e, V, tol_in, maxit - iters, false, true, &it_in);
+      else if (method == NDIAG_BICGSTAB)
+        si = bicgstab<float>(h, P, (float*)r64, e, V, tol_in, maxit - iters, false, true, &it_in);
+      else {
+        set_error("stationary method with fp32 precision is not supported");
+        return NDIAG_EINVAL;
+      }
+      iters += it_in;
+      if (si != NDIAG_OK && si != NDIAG_ENOCONV) {
+        st = si;
+        break;
+      }
+      ND_TRY(add_to(h, xd, e));
+    }
+    if (!dev_x) ND_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+  }
+  ND_CUDA(cudaStreamSynchronize(h->stream));
+  const ndiag_status ds = check_device_status(h);
+  if (ds != NDIAG_OK) st = ds;
+  if (info) {
+    info->iterations = iters;
+    info->outer = outer;
+    info->relres = relres;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    info->status = st;
+  }
+  return st;
+}

@@ -1,0 +1,275 @@
+// Symmetric SSOR apply on 2D 5-point matrices (Sec. 2: SSOR = a sweep and its
+// reverse; Sec. 5), SPD form for CG:
+//     z = w(2-w) (D + w L_J^T)^-1 D (D + w L_J)^-1 r .
+//
+// Forward half: the ordinary decomposed sweep of the forward phase with the
+// factor w(2-w) folded into beta.
+// Backward half, a transposed solve: cell i depends on every j with i in J_j.
+// Inside a subdomain that is the reversed wavefront (run by the sweep kernel
+// in the reversed frame, without twins, leaving out the start lines that border
+// coupled interfaces). The coupled pairs along an interface depend on the
+// interior cells of both subdomains and are solved afterwards, from the far
+// end of the interface back to its start vertex, one thread per interface;
+// the four start corners at a vertex form the 4x4 system of Eq. (2d:sor4b4),
+// solved by whichever of the vertex's four interface threads finishes last
+// (arrival counter, no waiting).
+#include "internal.h"
+
+namespace nd {
+namespace {
+
+template <class T, class TC>
+__device__ __forceinline__ T ldc(const TC* p) {
+  return (T)__ldcg(p);
+}
+template <>
+__device__ __forceinline__ float ldc<float, __half>(const __half* p) {
+  return __half2float(__ldcg(p));
+}
+
+template <class T, class TC>
+struct EdgeP {
+  int nx, ny;
+  Split sx, sy;
+  int base;
+  const TC* cT[4];  // transposed scaled entries, W E S N
+  const T* w;       // right-hand side of the backward solve
+  T* z;
+  T om;
+  unsigned* vcount;
+};
+
+template <class T, class TC>
+__device__ __forceinline__ T coef(const EdgeP<T, TC>& P, int e, int64_t i) {
+  return P.om * ldc<T, TC>(P.cT[e] + i);
+}
+
+template <class T>
+__device__ __forceinline__ void pair_solve(T ha, T gab, T hb, T gba, T& xa, T& xb) {
+  const T det = fma(-gab, gba, T(1));
+  xa = fma(-gab, hb, ha) / det;
+  xb = fma(-gba, ha, hb) / det;
+}
+
+template <class T>
+__device__ __forceinline__ void corner_solve(const T h[4], const T gx[4], const T gy[4], T x[4]) {
+  const T a11 = T(1) - gx[0] * gx[1] - gy[0] * gy[2];
+  const T a12 = -(gx[0] * gy[1] + gy[0] * gx[2]);
+  const T r1 = h[0] - gx[0] * h[1] - gy[0] * h[2];
+  const T a21 = -(gx[3] * gy[2] + gy[3] * gx[1]);
+  const T a22 = T(1) - gx[3] * gx[2] - gy[3] * gy[1];
+  const T r2 = h[3] - gx[3] * h[2] - gy[3] * h[1];
+  const T det = a11 * a22 - a12 * a21;
+  x[0] = (r1 * a22 - a12 * r2) / det;
+  x[3] = (a11 * r2 - a21 * r1) / det;
+  x[1] = h[1] - gx[1] * x[0] - gy[1] * x[3];
+  x[2] = h[2] - gx[2] * x[3] - gy[2] * x[0];
+}
+
+// 4x4 corner at interior vertex (vx, vy): slots k = (X + (k&1), Y + (k>>1)).
+template <class T, class TC>
+__device__ void solve_vertex(const EdgeP<T, TC>& P, int vx, int vy) {
+  const int X = P.sx.lo(vx + 1) - 1, Y = P.sy.lo(vy + 1) - 1;
+  T hh[4], gx[4], gy[4], xx[4];
+  int64_t idx[4];
+  for (int k = 0; k < 4; ++k) {
+    const int bx = k & 1, by = k >> 1;
+    const int cx = X + bx, cy = Y + by;
+    const int64_t i = (int64_t)cy * P.nx + cx;
+    idx[k] = i;
+    T hv = __ldcg(P.w + i);
+    // downstream neighbours inside the cell's own subdomain (away from the vertex)
+    const int ix = vx + bx, iy = vy + by;
+    if (P.sx.len(ix) >= 2) {
+      const int e = bx ? 1 : 0;  // E for the right column, W for the left one
+      hv = fma(-coef(P, e, i), __ldcg(P.z + i + (bx ? 1 : -1)), hv);
+    }
+    if (P.sy.len(iy) >= 2) {
+      const int e = by ? 3 : 2;
+      hv = fma(-coef(P, e, i), __ldcg(P.z + i + (by ? P.nx : -P.nx)), hv);
+    }
+    hh[k] = hv;
+    gx[k] = coef(P, bx ? 0 : 1, i);  // towards slot k^1
+    gy[k] = coef(P, by ? 2 : 3, i);  // towards slot k^2
+  }
+  corner_solve(hh, gx, gy, xx);
+  for (int k = 0; k < 4; ++k) P.z[idx[k]] = xx[k];
+}
+
+template <class T, class TC>
+__global__ void ssor_edges_kernel(EdgeP<T, TC> P) {
+  const int px = P.sx.p, py = P.sy.p;
+  const int ny_tasks = px * (py - 1), nx_tasks = (px - 1) * py;
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= ny_tasks + nx_tasks) return;
+  int vx = -1, vy = -1;
+  if (id < ny_tasks) {
+    // interface between (ix, iy) below and (ix, iy+1) above; pairs along x
+    const int ix = id % px, iy = id / px;
+    const int c = P.base ^ (ix & 1) ^ ((iy & 1) << 1);
+    if (!((c >> 1) & 1)) return;  // coupled only if both start here
+    const int cx = c & 1;
+    const int gx0 = P.sx.lo(ix), w = P.sx.len(ix);
+    const int Y = P.sy.lo(iy) + P.sy.len(iy) - 1;
+    const bool in_p = P.sy.len(iy) >= 2, in_q = P.sy.len(iy + 1) >= 2;
+    const int dx = cx ? -1 : 1;
+    const int ge = cx ? gx0 : gx0 + w - 1;  // far end of the chain
+    const bool corner = cx ? (gx0 + w < P.nx) : (gx0 > 0);
+    if (corner) {
+      vx = cx ? ix : ix - 1;
+      vy = iy;
+    }
+    // pairs from the far end back to the start; the start column belongs to
+    // the corner system when there is one
+    const int npairs = corner ? w - 1 : w;
+    T zp_next = T(0), zq_next = T(0);
+    for (int k = 0; k < npairs; ++k) {
+      const int gx = ge - k * dx;
+      const int64_t ip = (int64_t)Y * P.nx + gx, iq = ip + P.nx;
+      T hp = __ldcg(P.w + ip), hq = __ldcg(P.w + iq);
+      const int en = cx ? 0 : 1;  // entry towards the next cell along the chain
+      if (gx != ge) {
+        hp = fma(-coef(P, en, ip), zp_next, hp);
+        hq = fma(-coef(P, en, iq), zq_next, hq);
+      }
+      if (in_p) hp = fma(-coef(P, 2, ip), __ldcg(P.z + ip - P.nx), hp);
+      if (in_q) hq = fma(-coef(P, 3, iq), __ldcg(P.z + iq + P.nx), hq);
+      T zp, zq;
+      pair_solve(hp, coef(P, 3, ip), hq, coef(P, 2, iq), zp, zq);
+      P.z[ip] = zp;
+      P.z[iq] = zq;
+      zp_next = zp;
+      zq_next = zq;
+    }
+  } else {
+    // interface between (ix, iy) left and (ix+1, iy) right; pairs along y
+    const int k = id - ny_tasks;
+    const int ix = k % (px - 1), iy = k / (px - 1);
+    const int c = P.base ^ (ix & 1) ^ ((iy & 1) << 1);
+    if (!(c & 1)) return;
+    const int cy = (c >> 1) & 1;
+    const int gy0 = P.sy.lo(iy), h = P.sy.len(iy);
+    const int X = P.sx.lo(ix) + P.sx.len(ix) - 1;
+    const bool in_p = P.sx.len(ix) >= 2, in_q = P.sx.len(ix + 1) >= 2;
+    const int dy = cy ? -1 : 1;
+    const int ge = cy ? gy0 : gy0 + h - 1;
+    const bool corner = cy ? (gy0 + h < P.ny) : (gy0 > 0);
+    if (corner) {
+      vx = ix;
+      vy = cy ? iy : iy - 1;
+    }
+    const int npairs = corner ? h - 1 : h;
+    T zp_next = T(0), zq_next = T(0);
+    for (int k = 0; k < npairs; ++k) {
+      const int gy = ge - k * dy;
+      const int64_t ip = (int64_t)gy * P.nx + X, iq = ip + 1;
+      T hp = __ldcg(P.w + ip), hq = __ldcg(P.w + iq);
+      const int en = cy ? 2 : 3;
+      if (gy != ge) {
+        hp = fma(-coef(P, en, ip), zp_next, hp);
+        hq = fma(-coef(P, en, iq), zq_next, hq);
+      }
+      if (in_p) hp = fma(-coef(P, 0, ip), __ldcg(P.z + ip - 1), hp);
+      if (in_q) hq = fma(-coef(P, 1, iq), __ldcg(P.z + iq + 1), hq);
+      T zp, zq;
+      pair_solve(hp, coef(P, 1, ip), hq, coef(P, 0, iq), zp, zq);
+      P.z[ip] = zp;
+      P.z[iq] = zq;
+      zp_next = zp;
+      zq_next = zq;
+    }
+  }
+  if (vx >= 0) {
+    __threadfence();
+    const unsigned vid = (unsigned)(vx + (px - 1) * vy);
+    if (atomicAdd(&P.vcount[vid], 1u) == 3u) {
+      P.vcount[vid] = 0;  // ready for the next apply
+      __threadfence();
+      solve_vertex(P, vx, vy);
+    }
+  }
+}
+
+template <class TC>
+__global__ void transposed_set_kernel(int nx, int ny, int64_t N, const double* A, TC* out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx), y = (int)(i / nx);
+    const double inv = 1.0 / A[i];
+    out[i] = (TC)inv;
+    // entry e of row i points to j; the transposed entry is A(j, opposite of e)
+    const double w = x > 0 ? A[2 * N + i - 1] : 0.0;        // A(i-1, E)
+    const double e = x + 1 < nx ? A[1 * N + i + 1] : 0.0;   // A(i+1, W)
+    const double s = y > 0 ? A[4 * N + i - nx] : 0.0;       // A(i-nx, N)
+    const double n = y + 1 < ny ? A[3 * N + i + nx] : 0.0;  // A(i+nx, S)
+    out[1 * N + i] = (TC)(w * inv);
+    out[2 * N + i] = (TC)(e * inv);
+    out[3 * N + i] = (TC)(s * inv);
+    out[4 * N + i] = (TC)(n * inv);
+  }
+}
+
+template <class T, class TC>
+ndiag_status run_edges(Handle* h, int mode, double omega, const void* w, void* z) {
+  if (mode == NDIAG_NATURAL) return NDIAG_OK;  // one subdomain: no interfaces
+  EdgeP<T, TC> P{};
+  P.nx = (int)h->n[0];
+  P.ny = (int)h->n[1];
+  const int px = h->sub[0], py = h->sub[1];
+  P.sx = Split{px, P.nx / px, P.nx % px};
+  P.sy = Split{py, P.ny / py, P.ny % py};
+  P.base = base_corner(2, fwd_phase(2));
+  const size_t N = (size_t)h->N;
+  const TC* base = (const TC*)h->sorT.base;
+  for (int e = 0; e < 4; ++e) P.cT[e] = base + (1 + e) * N;
+  P.w = (const T*)w;
+  P.z = (T*)z;
+  P.om = (T)omega;
+  const int tasks = px * (py - 1) + (px - 1) * py;
+  if (tasks <= 0) return NDIAG_OK;
+  const size_t vbytes = sizeof(unsigned) * (size_t)((px - 1) * (py - 1) + 1);
+  if (h->vcount_bytes < vbytes) {
+    dev_free(h->vcount, h->vcount_bytes, h->stream);
+    h->vcount = (unsigned*)dev_alloc(vbytes, h->stream);
+    if (!h->vcount) return NDIAG_ENOMEM;
+    h->vcount_bytes = vbytes;
+    ND_CUDA(cudaMemsetAsync(h->vcount, 0, vbytes, h->stream));
+  }
+  P.vcount = h->vcount;
+  ++h->launches;
+  ssor_edges_kernel<T, TC><<<(tasks + 63) / 64, 64, 0, h->stream>>>(P);
+  ND_CUDA(cudaGetLastError());
+  return NDIAG_OK;
+}
+
+}  // namespace
+
+ndiag_status build_scaled_transposed(Handle* h, ScaledSet& set) {
+  const size_t cs = h->precision == NDIAG_FP64 ? 8 : h->precision == NDIAG_FP32 ? 4 : 2;
+  const size_t bytes = cs * (size_t)h->stencil * (size_t)h->N;
+  if (!set.base) {
+    set.base = dev_alloc(bytes, h->stream);
+    if (!set.base) return NDIAG_ENOMEM;
+    set.bytes = bytes;
+  }
+  const int nx = (int)h->n[0], ny = (int)h->n[1];
+  const int grid = h->sm_count * 4;
+  ++h->launches;
+  if (h->precision == NDIAG_FP64)
+    transposed_set_kernel<double><<<grid, 256, 0, h->stream>>>(nx, ny, h->N, h->A64, (double*)set.base);
+  else if (h->precision == NDIAG_FP32)
+    transposed_set_kernel<float><<<grid, 256, 0, h->stream>>>(nx, ny, h->N, h->A64, (float*)set.base);
+  else
+    transposed_set_kernel<__half><<<grid, 256, 0, h->stream>>>(nx, ny, h->N, h->A64, (__half*)set.base);
+  ND_CUDA(cudaGetLastError());
+  return NDIAG_OK;
+}
+
+ndiag_status launch_ssor_edges2d(Handle* h, int mode, double omega, const void* w, void* z) {
+  switch (h->precision) {
+    case NDIAG_FP64: return run_edges<double, double>(h, mode, omega, w, z);
+    case NDIAG_FP32: return run_edges<float, float>(h, mode, omega, w, z);
+    default: return run_edges<float, __half>(h, mode, omega, w, z);
+  }
+}
+
+}  // namespace nd

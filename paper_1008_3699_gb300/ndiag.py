@@ -1,0 +1,203 @@
+"""Python binding of libndiag.so (include/ndiag.h): argument marshalling only.
+
+Every step of a sweep, factorisation or solve runs in the CUDA library; this
+module converts torch tensors / numpy arrays to pointers and status codes to
+exceptions. Device memory that the library allocates comes from torch's
+caching allocator through the C allocator hook. There is no CPU fallback: if
+the library is missing, importing the binding's entry points fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libndiag.so")
+
+OK, EINVAL, ENOMEM, ENOCONV, EBREAKDOWN, EDEVICE, ETIMEOUT, EBUSY, ESTATE = range(9)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ENOCONV", "EBREAKDOWN", "EDEVICE", "ETIMEOUT", "EBUSY", "ESTATE"]
+FP64, FP32, FP32_D16 = 0, 1, 2
+PRECISION = {"fp64": FP64, "fp32": FP32, "fp32_d16": FP32_D16}
+NATURAL, DECOMPOSED = 0, 1
+PCG, BICGSTAB, STATIONARY = 0, 1, 2
+PREC_NONE, PREC_SSOR, PREC_ILU0 = 0, 1, 2
+
+# every symbol include/ndiag.h declares
+EXPORTED = ["ndiag_set_allocator", "ndiag_last_error", "ndiag_create", "ndiag_destroy", "ndiag_cells",
+            "ndiag_precision", "sor_sweep", "ssor_apply", "ilu0_factor", "ilu0_apply", "ndiag_residual",
+            "krylov_solve", "ndiag_profile", "ndiag_read_counters"]
+
+
+class NdiagError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"ndiag {name}: {msg}")
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer", ctypes.c_int), ("relres", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("sweep_launches", ctypes.c_int64), ("sweep_ms", ctypes.c_double),
+                ("sweep_bytes", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+_hooks = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libndiag.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path == LIB_PATH:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    P, I, L64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    L.ndiag_set_allocator.argtypes = [ALLOC_FN, FREE_FN, P]
+    L.ndiag_last_error.restype = ctypes.c_char_p
+    L.ndiag_create.argtypes = [ctypes.POINTER(P), I, P, I, P, P, I, P]
+    L.ndiag_destroy.argtypes = [P]
+    L.ndiag_destroy.restype = None
+    L.ndiag_cells.argtypes = [P]
+    L.ndiag_cells.restype = L64
+    L.ndiag_precision.argtypes = [P]
+    L.sor_sweep.argtypes = [P, I, P, L64, P, P, P]
+    L.ssor_apply.argtypes = [P, I, D, P, P]
+    L.ilu0_factor.argtypes = [P, I]
+    L.ilu0_apply.argtypes = [P, P, P]
+    L.ndiag_residual.argtypes = [P, P, P, P, ctypes.POINTER(D)]
+    L.krylov_solve.argtypes = [P, I, I, I, P, D, I, P, P, ctypes.POINTER(SolveInfo)]
+    L.ndiag_profile.argtypes = [P, I]
+    L.ndiag_read_counters.argtypes = [P, ctypes.POINTER(Counters)]
+    if path == LIB_PATH:
+        _lib = L
+    return L
+
+
+def _install_torch_allocator(L):
+    """Route the library's device allocations through torch's caching allocator."""
+    global _hooks
+    if _hooks is not None:
+        return
+    import torch
+
+    def alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:  # out of memory: the library reports NDIAG_ENOMEM
+            return None
+
+    def free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    _hooks = (ALLOC_FN(alloc), FREE_FN(free))
+    L.ndiag_set_allocator(_hooks[0], _hooks[1], None)
+
+
+def _check(L, status):
+    if status != OK:
+        raise NdiagError(status, L.ndiag_last_error().decode(errors="replace"))
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _omega(omega, dim):
+    v = np.atleast_1d(np.asarray(omega, dtype=np.float64)).ravel()
+    out = np.full(8, v[0]) if len(v) == 1 else np.zeros(8)
+    if len(v) > 1:
+        out[: len(v)] = v
+    return out
+
+
+class NDiag:
+    """A structured n-diagonal system resident on the current CUDA device."""
+
+    def __init__(self, dim, n, stencil, diags, sub=(1, 1, 1), precision="fp64", stream=None):
+        import torch
+        self.L = load()
+        _install_torch_allocator(self.L)
+        self.dim = int(dim)
+        self.n = tuple(int(v) for v in (list(n) + [1, 1, 1])[:3])
+        self.stencil = int(stencil)
+        self.N = int(np.prod(self.n[: self.dim]))
+        self.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        self.dtype = torch.float64 if self.precision == FP64 else torch.float32
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        d = np.ascontiguousarray(diags, dtype=np.float64).reshape(self.stencil, self.N)
+        n64 = np.array(self.n, dtype=np.int64)
+        sub32 = np.array((list(sub) + [1, 1, 1])[:3], dtype=np.int32)
+        self.sub = tuple(int(v) for v in sub32)
+        h = ctypes.c_void_p()
+        _check(self.L, self.L.ndiag_create(ctypes.byref(h), self.dim, _ptr(n64), self.stencil, _ptr(d),
+                                           _ptr(sub32), self.precision, ctypes.c_void_p(self.stream.cuda_stream)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ndiag_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty(self, dtype=None):
+        import torch
+        return torch.empty(self.N, dtype=dtype or self.dtype, device="cuda")
+
+    def sor_sweep(self, omega, t, b, x_old, x_new, mode=DECOMPOSED):
+        _check(self.L, self.L.sor_sweep(self.h, mode, _ptr(_omega(omega, self.dim)), int(t), _ptr(b),
+                                        _ptr(x_old), _ptr(x_new)))
+
+    def ssor_apply(self, omega, r, z, mode=DECOMPOSED):
+        _check(self.L, self.L.ssor_apply(self.h, mode, float(omega), _ptr(r), _ptr(z)))
+
+    def ilu0_factor(self, mode=DECOMPOSED):
+        _check(self.L, self.L.ilu0_factor(self.h, mode))
+
+    def ilu0_apply(self, r, z):
+        _check(self.L, self.L.ilu0_apply(self.h, _ptr(r), _ptr(z)))
+
+    def residual(self, b, x, r):
+        nrm = ctypes.c_double()
+        _check(self.L, self.L.ndiag_residual(self.h, _ptr(b), _ptr(x), _ptr(r), ctypes.byref(nrm)))
+        return nrm.value
+
+    def profile(self, enable=True):
+        """Reset the launch counters; with enable, time every sweep kernel."""
+        _check(self.L, self.L.ndiag_profile(self.h, 1 if enable else 0))
+
+    def counters(self):
+        c = Counters()
+        _check(self.L, self.L.ndiag_read_counters(self.h, ctypes.byref(c)))
+        return dict(launches=c.launches, sweep_launches=c.sweep_launches, sweep_ms=c.sweep_ms,
+                    sweep_bytes=c.sweep_bytes)
+
+    def solve(self, method, precond, b, x, rtol=1e-8, maxit=10000, omega=1.0, mode=DECOMPOSED,
+              raise_on_noconv=True):
+        """b, x: fp64 torch CUDA tensors or numpy arrays (host). x is updated."""
+        info = SolveInfo()
+        st = self.L.krylov_solve(self.h, method, precond, mode, _ptr(_omega(omega, self.dim)), float(rtol),
+                                 int(maxit), _ptr(b), _ptr(x), ctypes.byref(info))
+        if st != OK and (raise_on_noconv or st != ENOCONV):
+            _check(self.L, st)
+        return dict(iters=info.iterations, outer=info.outer, relres=info.relres, seconds=info.seconds,
+                    status=STATUS_NAMES[st])
