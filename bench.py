@@ -245,7 +245,7 @@ def main():
         hd.copy_(torch.from_numpy(problem["diags"]))
         hb_np, hx_np, hd_np = hb.numpy(), hx.numpy(), hd.numpy()
         e2e_updates, e2e_s = 0.0, 0.0
-        for k in range(args.e2e_steps + 1):
+        for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             g = nd.NDiag(2, problem["n"], 5, hd_np, problem["sub"], "fp64", stream=stream)
@@ -260,7 +260,8 @@ def main():
             if k > 0:  # first one warms the allocator
                 e2e_updates += float(N) * c2["sweep_launches"]
                 e2e_s += dt
-        e2e_val = torch.tensor([e2e_updates / e2e_s / 1e9 * world], dtype=torch.float64, device="cuda")
+        e2e_val = torch.tensor([e2e_updates / e2e_s / 1e9 * world if e2e_s > 0 else 0.0],
+                               dtype=torch.float64, device="cuda")
 
         natural = None
         if not args.no_natural and rank == 0:
