@@ -145,6 +145,31 @@ ndiag_status ilu0_factor(ndiag* h, int mode);
  * r, z DEVICE vectors (handle precision); z may alias r. ESTATE if not factored. */
 ndiag_status ilu0_apply(ndiag* h, const void* r, void* z);
 
+/*
+ * ilu0_apply_noalloc -- the same z = M^-1 r as ilu0_apply, for callers that
+ * cannot let the library allocate device memory during the call (device
+ * memory owned by another allocator or runtime, service loops that must not
+ * allocate once running, work replayed from a recorded command stream). The
+ * paper has no counterpart: this is an interface variant, not a method step.
+ * ilu0_apply allocates its scratch (the intermediate vector y and, for
+ * subdomains taller than one slab, the slab hand-off words) on first use; this
+ * entry point takes them from one fixed array in device memory instead,
+ * NDIAG_NOALLOC_MAX_CELLS cells of fp64 plus 64 Ki hand-off words (about
+ * 8.8 MiB), which every GPU that loads the library holds until the process
+ * exits. It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   r, z   DEVICE vectors (handle precision); z may alias r.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   with that device current; make that first call before any stream capture.
+ *   Sharing: every call uses the same array and leaves its contents behind
+ *   (the hand-off words are cleared by each call before use). Calls that
+ *   overlap on the GPU (other streams, threads or handles) race on it.
+ * Errors: NDIAG_EINVAL if N > NDIAG_NOALLOC_MAX_CELLS, for stencils other than
+ * 2D 5-point, or if a subdomain split needs more than 64 Ki hand-off words;
+ * NDIAG_ESTATE before ilu0_factor.
+ */
+#define NDIAG_NOALLOC_MAX_CELLS (1 << 20)
+ndiag_status ilu0_apply_noalloc(ndiag* h, const void* r, void* z);
+
 /* Residual r = b - A x in fp64 (A in fp64) and, if norm2 != NULL, ||r||_2
  * copied to the host (synchronises). b, x, r: DEVICE double vectors. */
 ndiag_status ndiag_residual(ndiag* h, const double* b, const double* x, double* r, double* norm2);

@@ -139,6 +139,9 @@ ndiag_status launch_sweep2d_ex(Handle* h, int kind, int mode, int64_t t, const d
                                const ScaledSet& set, const void* rhs, const void* xold, void* xnew,
                                double beta_scale, bool reverse_interior);
 ndiag_status launch_ssor_edges2d(Handle* h, int mode, double omega, const void* w, void* z);
+ndiag_status launch_tri_sweep2d_scratch(Handle* h, int kind, int mode, int64_t t, const ScaledSet& set,
+                                        const void* rhs, void* xnew, unsigned* sync, size_t sync_bytes,
+                                        void* twin, size_t twin_bytes);
 ndiag_status build_scaled(Handle* h, ScaledSet& set, const double* piv);
 ndiag_status build_scaled_transposed(Handle* h, ScaledSet& set);
 

@@ -437,6 +437,78 @@ ndiag_status launch_sweep2d(Handle* h, int kind, int mode, int64_t t, const doub
   return launch_sweep2d_ex(h, kind, mode, t, omega, set, rhs, xold, xnew, 1.0, false);
 }
 
+namespace {
+
+// A triangular sweep (KIND_TRI_SCALED / KIND_TRI_UNIT, unit relaxation) whose
+// slab hand-off words live in caller-provided device memory instead of the
+// handle's lazily allocated buffers. Allocates nothing.
+template <class T, class TC>
+ndiag_status tri_sweep_in_scratch(Handle* h, int kind, int mode, int64_t t, const ScaledSet& set,
+                                  const void* rhs, void* xnew, unsigned* sync, size_t sync_bytes,
+                                  void* twin, size_t twin_bytes) {
+  SweepP<T, TC> P{};
+  P.bscale = T(1);
+  P.rev = 0;
+  P.nx = (int)h->n[0];
+  P.ny = (int)h->n[1];
+  const bool nat = mode == NDIAG_NATURAL || mode == MODE_NATURAL_REV;
+  const int px = nat ? 1 : h->sub[0], py = nat ? 1 : h->sub[1];
+  P.sx = Split{px, P.nx / px, P.nx % px};
+  P.sy = Split{py, P.ny / py, P.ny % py};
+  P.base = nat ? (mode == MODE_NATURAL_REV ? 3 : 0) : base_corner(2, t);
+  P.coupled = nat ? 0 : 1;
+  const int bands = (P.sy.len(0) + BH - 1) / BH;
+  P.spp = (bands + NW - 1) / NW;
+  P.use_ticket = P.spp > 1;
+  const size_t N = (size_t)h->N;
+  const TC* base = (const TC*)set.base;
+  P.inv = base;
+  for (int e = 0; e < 4; ++e) P.c[e] = base + (size_t)(1 + e) * N;
+  P.rhs = (const T*)rhs;
+  P.xold = nullptr;
+  P.xnew = (T*)xnew;
+  P.A = h->A64;
+  for (int k = 0; k < 4; ++k) P.om[k] = T(1);
+  const unsigned nslabs = (unsigned)(px * py * P.spp);
+  if (P.use_ticket) {
+    const size_t need = sizeof(unsigned) * (1 + (size_t)nslabs);
+    if (need > sync_bytes || sizeof(T) * (size_t)nslabs > twin_bytes) return NDIAG_EINVAL;
+    ND_CUDA(cudaMemsetAsync(sync, 0, need, h->stream));  // hand-off words start at zero
+    P.ticket = sync;
+    P.flags = sync + 1;
+    P.twin_hand = (T*)twin;
+  }
+  P.st = h->status;
+  ++h->launches;
+  ++h->sweep_launches;
+  if (kind == KIND_TRI_SCALED)
+    sweep2d_kernel<T, TC, KIND_TRI_SCALED><<<nslabs, NW * 32, 0, h->stream>>>(P);
+  else
+    sweep2d_kernel<T, TC, KIND_TRI_UNIT><<<nslabs, NW * 32, 0, h->stream>>>(P);
+  ND_CUDA(cudaGetLastError());
+  return NDIAG_OK;
+}
+
+}  // namespace
+
+ndiag_status launch_tri_sweep2d_scratch(Handle* h, int kind, int mode, int64_t t, const ScaledSet& set,
+                                        const void* rhs, void* xnew, unsigned* sync, size_t sync_bytes,
+                                        void* twin, size_t twin_bytes) {
+  if (kind != KIND_TRI_SCALED && kind != KIND_TRI_UNIT) return NDIAG_EINVAL;
+  switch (h->precision) {
+    case NDIAG_FP64:
+      return tri_sweep_in_scratch<double, double>(h, kind, mode, t, set, rhs, xnew, sync, sync_bytes, twin,
+                                                  twin_bytes);
+    case NDIAG_FP32:
+      return tri_sweep_in_scratch<float, float>(h, kind, mode, t, set, rhs, xnew, sync, sync_bytes, twin,
+                                                twin_bytes);
+    case NDIAG_FP32_D16:
+      return tri_sweep_in_scratch<float, __half>(h, kind, mode, t, set, rhs, xnew, sync, sync_bytes, twin,
+                                                 twin_bytes);
+  }
+  return NDIAG_EINVAL;
+}
+
 // d~ of the decomposed (or natural) ILU(0), written to `out` (fp64, N): the
 // same wavefront without interface coupling, since a mutual pair contributes
 // no elimination term (Sec. 5).

@@ -27,7 +27,8 @@ PREC_NONE, PREC_SSOR, PREC_ILU0 = 0, 1, 2
 # every symbol include/ndiag.h declares
 EXPORTED = ["ndiag_set_allocator", "ndiag_last_error", "ndiag_create", "ndiag_destroy", "ndiag_cells",
             "ndiag_precision", "sor_sweep", "ssor_apply", "ilu0_factor", "ilu0_apply", "ndiag_residual",
-            "krylov_solve", "ndiag_profile", "ndiag_read_counters"]
+            "krylov_solve", "ndiag_profile", "ndiag_read_counters", "ilu0_apply_noalloc"]
+NOALLOC_MAX_CELLS = 1 << 20
 
 
 class NdiagError(RuntimeError):
@@ -75,6 +76,7 @@ def load(path: str = LIB_PATH):
     L.ssor_apply.argtypes = [P, I, D, P, P]
     L.ilu0_factor.argtypes = [P, I]
     L.ilu0_apply.argtypes = [P, P, P]
+    L.ilu0_apply_noalloc.argtypes = [P, P, P]
     L.ndiag_residual.argtypes = [P, P, P, P, ctypes.POINTER(D)]
     L.krylov_solve.argtypes = [P, I, I, I, P, D, I, P, P, ctypes.POINTER(SolveInfo)]
     L.ndiag_profile.argtypes = [P, I]
@@ -175,6 +177,10 @@ class NDiag:
 
     def ilu0_apply(self, r, z):
         _check(self.L, self.L.ilu0_apply(self.h, _ptr(r), _ptr(z)))
+
+    def ilu0_apply_noalloc(self, r, z):
+        """ilu0_apply without device allocation (fixed scratch inside the library)."""
+        _check(self.L, self.L.ilu0_apply_noalloc(self.h, _ptr(r), _ptr(z)))
 
     def residual(self, b, x, r):
         nrm = ctypes.c_double()
