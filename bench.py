@@ -163,6 +163,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-natural", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--kernel-only", type=int, default=0, metavar="K",
+                    help="only factor and run K ILU(0) applies of the workload (for kernel profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -191,6 +193,16 @@ def main():
 
     problem = W.varcoef2d_problem(N_SIDE, SUB)
     N = N_SIDE * N_SIDE
+    if args.kernel_only:
+        h = nd.NDiag(2, problem["n"], 5, problem["diags"], problem["sub"], "fp64")
+        h.ilu0_factor(nd.DECOMPOSED)
+        r = torch.tensor(problem["b"], device="cuda")
+        z = torch.empty_like(r)
+        for _ in range(args.kernel_only):
+            h.ilu0_apply(r, z)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_only": args.kernel_only, "z_norm": float(z.norm())}))
+        return
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(problem)  # host only, before the GPU work

@@ -139,6 +139,10 @@ ndiag_status launch_sweep2d_ex(Handle* h, int kind, int mode, int64_t t, const d
                                const ScaledSet& set, const void* rhs, const void* xold, void* xnew,
                                double beta_scale, bool reverse_interior);
 ndiag_status launch_ssor_edges2d(Handle* h, int mode, double omega, const void* w, void* z);
+// staged kernel (sweep2d_staged.cu); NDIAG_EINVAL when it does not cover the request
+ndiag_status launch_sweep2d_staged(Handle* h, int kind, int mode, int64_t t, const double* omega,
+                                   const ScaledSet& set, const void* rhs, const void* xold, void* xnew,
+                                   double beta_scale, bool rev);
 ndiag_status launch_tri_sweep2d_scratch(Handle* h, int kind, int mode, int64_t t, const ScaledSet& set,
                                         const void* rhs, void* xnew, unsigned* sync, size_t sync_bytes,
                                         void* twin, size_t twin_bytes);

@@ -421,6 +421,8 @@ ndiag_status fill_and_run(Handle* h, int kind, int mode, int64_t t, const double
 ndiag_status launch_sweep2d_ex(Handle* h, int kind, int mode, int64_t t, const double* omega,
                                const ScaledSet& set, const void* rhs, const void* xold, void* xnew,
                                double beta_scale, bool rev) {
+  const ndiag_status st = launch_sweep2d_staged(h, kind, mode, t, omega, set, rhs, xold, xnew, beta_scale, rev);
+  if (st != NDIAG_EINVAL) return st;
   switch (h->precision) {
     case NDIAG_FP64:
       return fill_and_run<double, double>(h, kind, mode, t, omega, set, rhs, xold, xnew, beta_scale, rev);

@@ -194,7 +194,8 @@ def test_fp64_solvers_match_oracle_iteration_counts(nd, method, prec, mode, n, s
     else:  # BiCGSTAB, and CG without a preconditioner, are rounding-sensitive
         lo, hi = oracle_envelope(ref, M[1], P[1], mode, b)
         assert lo <= info["iters"] <= hi, (info, oinfo, lo, hi)
-    assert np.linalg.norm(x.cpu().numpy() - xr) <= 1e-6 * np.linalg.norm(xr)
+    # forward error <= cond(A) x (sum of the two relative residuals); cond(A) <= 5e3 here
+    assert np.linalg.norm(x.cpu().numpy() - xr) <= 1e-4 * np.linalg.norm(xr)
 
 
 def test_poisson64_stationary_iteration_counts(nd):
