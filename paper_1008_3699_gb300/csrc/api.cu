@@ -137,6 +137,7 @@ ndiag_status build_scaled(Handle* h, ScaledSet& set, const double* piv) {
   }
   const int grid = h->sm_count * 4;
   ++h->launches;
+  ++set.version;
   switch (h->precision) {
     case NDIAG_FP64:
       scaled_set_kernel<double><<<grid, 256, 0, h->stream>>>(h->N, h->stencil, h->A64, piv, (double*)set.base);
@@ -337,6 +338,7 @@ void ndiag_destroy(ndiag* h) {
   dev_free(h->vcount, h->vcount_bytes, s);
   dev_free(h->sync, h->sync_bytes, s);
   dev_free(h->twin_hand, h->twin_hand_bytes, s);
+  for (LineTable& t : h->line_tables) dev_free(t.buf, t.bytes, s);
   dev_free(h->status, sizeof(DevStatus), s);
   dev_free(h->kws.p, h->kws.bytes, s);
   dev_free(h->red, h->red_bytes, s);

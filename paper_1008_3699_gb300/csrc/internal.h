@@ -51,7 +51,22 @@ enum SweepKind {
 struct ScaledSet {
   void* base = nullptr;  // one allocation: s arrays of N values (inv, then entries 1..s-1)
   size_t bytes = 0;
+  unsigned version = 0;  // bumped whenever the values change (invalidates line tables)
 };
+
+// Coefficients of the coupled start lines of one sweep phase (2D): for every
+// subdomain with a coupled start row / column and every position along it,
+// the pair terms of Eq. 2d:sor2b2 that do not depend on the right-hand side.
+struct LineTable {
+  const void* set_base = nullptr;
+  unsigned set_version = 0;
+  int base = -1;          // start corner of subdomain 0
+  int om1 = 1;
+  double om[4] = {1, 1, 1, 1};
+  void* buf = nullptr;
+  size_t bytes = 0;
+};
+
 
 // Device-side status words (error flag written by bounded waits).
 struct DevStatus {
@@ -92,6 +107,7 @@ struct Handle {
   size_t sync_bytes = 0;
   void* twin_hand = nullptr;
   size_t twin_hand_bytes = 0;
+  std::vector<LineTable> line_tables;  // per (coefficient set, phase, relaxation)
   DevStatus* status = nullptr;   // device
 
   // Krylov workspace (allocated on first use)

@@ -254,6 +254,7 @@ ndiag_status build_scaled_transposed(Handle* h, ScaledSet& set) {
   const int nx = (int)h->n[0], ny = (int)h->n[1];
   const int grid = h->sm_count * 4;
   ++h->launches;
+  ++set.version;
   if (h->precision == NDIAG_FP64)
     transposed_set_kernel<double><<<grid, 256, 0, h->stream>>>(nx, ny, h->N, h->A64, (double*)set.base);
   else if (h->precision == NDIAG_FP32)

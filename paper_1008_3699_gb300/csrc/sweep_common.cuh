@@ -62,6 +62,42 @@ __device__ __noinline__ bool wait_gmem(const unsigned* p, unsigned v, DevStatus*
   return true;
 }
 
+// mbarrier (shared memory, CTA scope): one arrival completes a phase. A waiter
+// of the k-th completion (k = 0, 1, ...) tests parity k & 1.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mb_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mb_arrive(unsigned long long* b) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(b))
+               : "memory");
+}
+__device__ __forceinline__ bool mb_try(unsigned long long* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for a phase of an mbarrier (the hardware suspends the thread
+// between tests); records a timeout in the status word and returns false.
+__device__ __noinline__ bool mb_wait_slow(unsigned long long* b, unsigned parity, DevStatus* st) {
+  const long long t0 = clock64();
+  while (!mb_try(b, parity)) {
+    if (clock64() - t0 > WAIT_CYCLES) {
+      atomicExch(&st->timeout, 1);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ bool mb_wait(unsigned long long* b, unsigned parity, DevStatus* st) {
+  return mb_try(b, parity) || mb_wait_slow(b, parity, st);
+}
+
 // Asynchronous 4- or 8-byte copy global -> shared (cp.async, L1-allocating).
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
