@@ -42,7 +42,7 @@ def _stale(out: str, deps: list[str]) -> bool:
 def build(force: bool = False, verbose: bool = False, extra: tuple[str, ...] = ()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "ndiag.h"))
     objs, jobs = [], []
     for src in sources():

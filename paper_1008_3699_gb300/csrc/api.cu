@@ -189,8 +189,12 @@ ndiag_status do_ilu_apply(Handle* h, const void* r, void* z) {
   ND_TRY(ensure_tmp(h));
   const int64_t tf = fwd_phase(h->dim);
   // (D~ + L_J) y = r ; (D~ + U_J) z = D~ y   (U_J = implicit set of the reverse phase)
-  ND_TRY(launch_sweep2d(h, KIND_TRI_SCALED, h->ilu_mode, tf, nullptr, h->ilu, r, nullptr, h->tmp));
   const int back = h->ilu_mode == NDIAG_NATURAL ? (int)MODE_NATURAL_REV : h->ilu_mode;
+  if (h->dim == 3) {
+    ND_TRY(launch_sweep3d(h, KIND_TRI_SCALED, h->ilu_mode, tf, nullptr, h->ilu, r, nullptr, h->tmp, 1.0, false));
+    return launch_sweep3d(h, KIND_TRI_UNIT, back, tf ^ 1, nullptr, h->ilu, h->tmp, nullptr, z, 1.0, false);
+  }
+  ND_TRY(launch_sweep2d(h, KIND_TRI_SCALED, h->ilu_mode, tf, nullptr, h->ilu, r, nullptr, h->tmp));
   ND_TRY(launch_sweep2d(h, KIND_TRI_UNIT, back, tf ^ 1, nullptr, h->ilu, h->tmp, nullptr, z));
   return NDIAG_OK;
 }
@@ -207,6 +211,12 @@ ndiag_status do_ssor_apply(Handle* h, int mode, double omega, const void* r, voi
   if (!h->sorT.base) ND_TRY(build_scaled_transposed(h, h->sorT));
   const double om[8] = {omega, omega, omega, omega, omega, omega, omega, omega};
   const int64_t tf = fwd_phase(h->dim);
+  if (h->dim == 3) {
+    // forward: tmp = w(2-w) (D + w L_J)^-1 r ; then (D + w L_J^T) z = D tmp
+    ND_TRY(launch_sweep3d(h, KIND_TRI_SCALED, mode, tf, om, h->sor, r, nullptr, h->tmp, omega * (2.0 - omega),
+                          false));
+    return launch_sweep3d(h, KIND_TRI_UNIT, mode, tf, om, h->sorT, h->tmp, nullptr, z, 1.0, true);
+  }
   // forward: tmp = w(2-w) (D + w L_J)^-1 r
   ND_TRY(launch_sweep2d_ex(h, KIND_TRI_SCALED, mode, tf, om, h->sor, r, nullptr, h->tmp,
                            omega * (2.0 - omega), false));
@@ -260,7 +270,7 @@ ndiag_status ndiag_create(ndiag** out, int dim, const int64_t n[3], int stencil,
       set_error("diagonal entries must be positive");
       return NDIAG_EINVAL;
     }
-  if (stencil != 5) {
+  if (stencil == 9) {
     set_error("stencil not supported by this build yet");
     return NDIAG_EINVAL;
   }
@@ -383,6 +393,7 @@ ndiag_status sor_sweep(ndiag* h, int mode, const double* omega, int64_t t, const
                        void* x_new) {
   if (!h || !omega || !b || !x_old || !x_new || x_old == x_new) return NDIAG_EINVAL;
   if (mode != NDIAG_NATURAL && mode != NDIAG_DECOMPOSED) return NDIAG_EINVAL;
+  if (h->dim == 3) return launch_sweep3d(h, KIND_SOR, mode, t, omega, h->sor, b, x_old, x_new, 1.0, false);
   return launch_sweep2d(h, KIND_SOR, mode, t, omega, h->sor, b, x_old, x_new);
 }
 
@@ -390,7 +401,8 @@ ndiag_status ilu0_factor(ndiag* h, int mode) {
   if (!h || (mode != NDIAG_NATURAL && mode != NDIAG_DECOMPOSED)) return NDIAG_EINVAL;
   double* dt = (double*)dev_alloc(sizeof(double) * (size_t)h->N, h->stream);
   if (!dt) return NDIAG_ENOMEM;
-  ndiag_status st = launch_ilu_factor2d_into(h, mode, dt);
+  ndiag_status st =
+      h->dim == 3 ? launch_ilu_factor3d_into(h, mode, dt) : launch_ilu_factor2d_into(h, mode, dt);
   if (st == NDIAG_OK) st = build_scaled(h, h->ilu, dt);
   dev_free(dt, sizeof(double) * (size_t)h->N, h->stream);
   if (st == NDIAG_OK) st = check_status(h);

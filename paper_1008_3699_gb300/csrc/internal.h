@@ -163,6 +163,10 @@ ndiag_status launch_tri_sweep2d_scratch(Handle* h, int kind, int mode, int64_t t
                                         const void* rhs, void* xnew, unsigned* sync, size_t sync_bytes,
                                         void* twin, size_t twin_bytes);
 ndiag_status build_scaled(Handle* h, ScaledSet& set, const double* piv);
+// 3D 7-point sweeps by levels (sweep3d.cu); `transposed` solves (D + w L^T) y = v
+ndiag_status launch_sweep3d(Handle* h, int kind, int mode, int64_t t, const double* omega, const ScaledSet& set,
+                            const void* rhs, const void* xold, void* xnew, double beta_scale, bool transposed);
+ndiag_status launch_ilu_factor3d_into(Handle* h, int mode, double* out);
 ndiag_status build_scaled_transposed(Handle* h, ScaledSet& set);
 
 // BLAS-1 and SpMV (blas.cu)

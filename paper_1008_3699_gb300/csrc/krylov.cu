@@ -224,7 +224,10 @@ ndiag_status stationary(Handle* h, int mode, const double* omega, const T* b, T*
   T* cur = x;
   T* nxt = xalt;
   while (rel > tol_abs && it < maxit) {
-    ND_TRY(launch_sweep2d(h, KIND_SOR, mode, it, omega, h->sor, b, cur, nxt));
+    if (h->dim == 3)
+      ND_TRY(launch_sweep3d(h, KIND_SOR, mode, it, omega, h->sor, b, cur, nxt, 1.0, false));
+    else
+      ND_TRY(launch_sweep2d(h, KIND_SOR, mode, it, omega, h->sor, b, cur, nxt));
     ++it;
     if (sizeof(T) == 8) {
       ND_TRY(residual64(h, (const double*)b, (const double*)nxt, (double*)r, sc + SC_R0));

@@ -191,20 +191,27 @@ __global__ void ssor_edges_kernel(EdgeP<T, TC> P) {
 }
 
 template <class TC>
-__global__ void transposed_set_kernel(int nx, int ny, int64_t N, const double* A, TC* out) {
+__global__ void transposed_set_kernel(int nx, int ny, int nz, int s, int64_t N, const double* A, TC* out) {
+  const int64_t pl = (int64_t)nx * ny;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % nx), y = (int)(i / nx);
+    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / pl);
     const double inv = 1.0 / A[i];
     out[i] = (TC)inv;
     // entry e of row i points to j; the transposed entry is A(j, opposite of e)
     const double w = x > 0 ? A[2 * N + i - 1] : 0.0;        // A(i-1, E)
     const double e = x + 1 < nx ? A[1 * N + i + 1] : 0.0;   // A(i+1, W)
-    const double s = y > 0 ? A[4 * N + i - nx] : 0.0;       // A(i-nx, N)
+    const double so = y > 0 ? A[4 * N + i - nx] : 0.0;      // A(i-nx, N)
     const double n = y + 1 < ny ? A[3 * N + i + nx] : 0.0;  // A(i+nx, S)
     out[1 * N + i] = (TC)(w * inv);
     out[2 * N + i] = (TC)(e * inv);
-    out[3 * N + i] = (TC)(s * inv);
+    out[3 * N + i] = (TC)(so * inv);
     out[4 * N + i] = (TC)(n * inv);
+    if (s == 7) {
+      const double b = z > 0 ? A[6 * N + i - pl] : 0.0;       // A(i-pl, F)
+      const double f = z + 1 < nz ? A[5 * N + i + pl] : 0.0;  // A(i+pl, B)
+      out[5 * N + i] = (TC)(b * inv);
+      out[6 * N + i] = (TC)(f * inv);
+    }
   }
 }
 
@@ -251,16 +258,16 @@ ndiag_status build_scaled_transposed(Handle* h, ScaledSet& set) {
     if (!set.base) return NDIAG_ENOMEM;
     set.bytes = bytes;
   }
-  const int nx = (int)h->n[0], ny = (int)h->n[1];
+  const int nx = (int)h->n[0], ny = (int)h->n[1], nz = (int)h->n[2];
   const int grid = h->sm_count * 4;
   ++h->launches;
   ++set.version;
   if (h->precision == NDIAG_FP64)
-    transposed_set_kernel<double><<<grid, 256, 0, h->stream>>>(nx, ny, h->N, h->A64, (double*)set.base);
+    transposed_set_kernel<double><<<grid, 256, 0, h->stream>>>(nx, ny, nz, h->stencil, h->N, h->A64, (double*)set.base);
   else if (h->precision == NDIAG_FP32)
-    transposed_set_kernel<float><<<grid, 256, 0, h->stream>>>(nx, ny, h->N, h->A64, (float*)set.base);
+    transposed_set_kernel<float><<<grid, 256, 0, h->stream>>>(nx, ny, nz, h->stencil, h->N, h->A64, (float*)set.base);
   else
-    transposed_set_kernel<__half><<<grid, 256, 0, h->stream>>>(nx, ny, h->N, h->A64, (__half*)set.base);
+    transposed_set_kernel<__half><<<grid, 256, 0, h->stream>>>(nx, ny, nz, h->stencil, h->N, h->A64, (__half*)set.base);
   ND_CUDA(cudaGetLastError());
   return NDIAG_OK;
 }

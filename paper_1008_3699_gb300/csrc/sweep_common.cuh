@@ -33,7 +33,7 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
 // Bounded wait until *p >= v (warp-uniform), sleeping between polls so that
 // the waiting warp does not take issue slots from the producer. Returns false
 // on timeout after recording it in the status word.
-__device__ __noinline__ bool wait_smem(const volatile int* p, int v, DevStatus* st) {
+static __device__ __noinline__ bool wait_smem(const volatile int* p, int v, DevStatus* st) {
   if (*p >= v) {
     __threadfence_block();
     return true;
@@ -49,7 +49,7 @@ __device__ __noinline__ bool wait_smem(const volatile int* p, int v, DevStatus* 
   __threadfence_block();
   return true;
 }
-__device__ __noinline__ bool wait_gmem(const unsigned* p, unsigned v, DevStatus* st) {
+static __device__ __noinline__ bool wait_gmem(const unsigned* p, unsigned v, DevStatus* st) {
   if (ld_acquire(p) >= v) return true;
   const long long t0 = clock64();
   while (ld_acquire(p) < v) {
@@ -84,7 +84,7 @@ __device__ __forceinline__ bool mb_try(unsigned long long* b, unsigned parity) {
 }
 // Bounded wait for a phase of an mbarrier (the hardware suspends the thread
 // between tests); records a timeout in the status word and returns false.
-__device__ __noinline__ bool mb_wait_slow(unsigned long long* b, unsigned parity, DevStatus* st) {
+static __device__ __noinline__ bool mb_wait_slow(unsigned long long* b, unsigned parity, DevStatus* st) {
   const long long t0 = clock64();
   while (!mb_try(b, parity)) {
     if (clock64() - t0 > WAIT_CYCLES) {
