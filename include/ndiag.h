@@ -225,6 +225,40 @@ ndiag_status ndiag_profile(ndiag* h, int enable);
 /* Synchronises the handle's stream and reports the counters. */
 ndiag_status ndiag_read_counters(ndiag* h, ndiag_counters* out);
 
+/*
+ * Batched solves of many independent 2D 5-point problems (the paper has no
+ * counterpart: a GPU serving pattern around its decomposed SSOR). Each problem
+ * is a diagonal-major matrix (5 x nx[p]*ny[p], HOST, caller keeps ownership);
+ * all vectors of the batch are concatenated in problem order (problem p's
+ * cells after those of problems 0..p-1).
+ *   ndiag_batch_create   copies the matrices (fp32 sweeps, fp64 matrix for
+ *                        residuals); tile[p] = side of the square subdomains of
+ *                        problem p (NULL: 64; sides of at most 128); omega =
+ *                        SSOR factor; stream NULL = a stream of its own.
+ *   ndiag_batch_autotune chooses one tile side for the whole batch from
+ *                        {32, 64, 128}: batched SSOR apply time x pilot CG
+ *                        iterations (b: DEVICE, concatenated right-hand sides).
+ *   ndiag_batch_tiles    reports the tile side of every problem.
+ *   ndiag_batch_solve    FP32 SSOR-PCG with FP64 refinement of every problem
+ *                        to ||b - A x|| / ||b|| <= rtol (maxit inner
+ *                        iterations per refinement step); b, x DEVICE double,
+ *                        concatenated; x holds the initial guess; infos[p]
+ *                        (HOST, count entries) per problem. Every step of an
+ *                        iteration is one launch over all problems; chunks of
+ *                        iterations are replayed from a captured CUDA graph.
+ *                        NDIAG_ENOCONV if some problem missed rtol.
+ */
+typedef struct ndiag_batch ndiag_batch;
+ndiag_status ndiag_batch_create(ndiag_batch** out, int count, const int64_t* nx, const int64_t* ny,
+                                const double* const* diags, const int* tile, double omega, void* stream);
+ndiag_status ndiag_batch_autotune(ndiag_batch* b, const double* rhs);
+ndiag_status ndiag_batch_tiles(const ndiag_batch* b, int* tile);
+ndiag_status ndiag_batch_solve(ndiag_batch* b, double rtol, int maxit, const double* rhs, double* x,
+                               ndiag_solve_info* infos);
+int64_t ndiag_batch_cells(const ndiag_batch* b);
+int64_t ndiag_batch_launches(const ndiag_batch* b);
+void ndiag_batch_destroy(ndiag_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

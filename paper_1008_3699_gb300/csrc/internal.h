@@ -163,6 +163,38 @@ ndiag_status launch_tri_sweep2d_scratch(Handle* h, int kind, int mode, int64_t t
                                         const void* rhs, void* xnew, unsigned* sync, size_t sync_bytes,
                                         void* twin, size_t twin_bytes);
 ndiag_status build_scaled(Handle* h, ScaledSet& set, const double* piv);
+// One prepared launch of the staged 2D sweep over several handles (a batch of
+// independent problems): device arrays of per-problem parameters and slab
+// offsets, rebuilt by batch_sweep_prepare, launched by batch_sweep_launch
+// (graph-capturable: no host work).
+struct BatchSweep {
+  int precision = 0, kind = 0, np = 0;
+  bool om1 = true;
+  unsigned total = 0;  // slabs (CTAs) of the launch
+  double bytes = 0.0;  // algorithmic bytes of one launch
+  void* params = nullptr;
+  size_t params_bytes = 0;
+  unsigned* off = nullptr;
+  size_t off_bytes = 0;
+  std::vector<unsigned char> host_params;
+  std::vector<unsigned> host_off;
+};
+// set_sel: 0 SOR set, 1 ILU(0) set, 2 transposed SOR set
+ndiag_status batch_sweep_prepare(BatchSweep& b, Handle* const* hs, int np, int kind, int mode, int64_t t,
+                                 const double* omega, int set_sel, const void* const* rhs, const void* const* xold,
+                                 void* const* xnew, double beta_scale, bool rev, cudaStream_t s);
+ndiag_status batch_sweep_launch(const BatchSweep& b, cudaStream_t s);
+void batch_sweep_free(BatchSweep& b, cudaStream_t s);
+// the SSOR interface chains of several handles in one launch (ssor2d.cu)
+ndiag_status batch_edges_prepare(BatchSweep& b, Handle* const* hs, int np, double omega, const void* const* w,
+                                 void* const* z, cudaStream_t s);
+ndiag_status batch_edges_launch(const BatchSweep& b, cudaStream_t s);
+
+// Device status of a handle, read after a batch of launches (api.cu)
+ndiag_status check_device_status(Handle* h);
+// Re-partition a handle into sub[] subdomains (batch.cu, the autotuner)
+void handle_set_sub(Handle* h, const int sub[3]);
+
 // 3D 7-point sweeps by levels (sweep3d.cu); `transposed` solves (D + w L^T) y = v
 ndiag_status launch_sweep3d(Handle* h, int kind, int mode, int64_t t, const double* omega, const ScaledSet& set,
                             const void* rhs, const void* xold, void* xnew, double beta_scale, bool transposed);

@@ -13,6 +13,10 @@
 // the four start corners at a vertex form the 4x4 system of Eq. (2d:sor4b4),
 // solved by whichever of the vertex's four interface threads finishes last
 // (arrival counter, no waiting).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "internal.h"
 
 namespace nd {
@@ -97,10 +101,9 @@ __device__ void solve_vertex(const EdgeP<T, TC>& P, int vx, int vy) {
 }
 
 template <class T, class TC>
-__global__ void ssor_edges_kernel(EdgeP<T, TC> P) {
+__device__ __forceinline__ void edges_body(const EdgeP<T, TC>& P, int id) {
   const int px = P.sx.p, py = P.sy.p;
   const int ny_tasks = px * (py - 1), nx_tasks = (px - 1) * py;
-  const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= ny_tasks + nx_tasks) return;
   int vx = -1, vy = -1;
   if (id < ny_tasks) {
@@ -216,9 +219,27 @@ __global__ void transposed_set_kernel(int nx, int ny, int nz, int s, int64_t N, 
 }
 
 template <class T, class TC>
-ndiag_status run_edges(Handle* h, int mode, double omega, const void* w, void* z) {
-  if (mode == NDIAG_NATURAL) return NDIAG_OK;  // one subdomain: no interfaces
-  EdgeP<T, TC> P{};
+__global__ void ssor_edges_kernel(EdgeP<T, TC> P) {
+  edges_body(P, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// The interface chains of several problems: problem p owns blocks
+// off[p] .. off[p+1] - 1 (64 threads each).
+template <class T, class TC>
+__global__ void ssor_edges_batch_kernel(const EdgeP<T, TC>* __restrict__ Pa, const unsigned* __restrict__ off,
+                                        int np) {
+  int lo = 0, hi = np - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  edges_body(Pa[lo], (int)(blockIdx.x - off[lo]) * blockDim.x + threadIdx.x);
+}
+
+template <class T, class TC>
+ndiag_status edge_params(Handle* h, double omega, const void* w, void* z, EdgeP<T, TC>& P, int& tasks) {
+  P = EdgeP<T, TC>{};
   P.nx = (int)h->n[0];
   P.ny = (int)h->n[1];
   const int px = h->sub[0], py = h->sub[1];
@@ -231,7 +252,7 @@ ndiag_status run_edges(Handle* h, int mode, double omega, const void* w, void* z
   P.w = (const T*)w;
   P.z = (T*)z;
   P.om = (T)omega;
-  const int tasks = px * (py - 1) + (px - 1) * py;
+  tasks = px * (py - 1) + (px - 1) * py;
   if (tasks <= 0) return NDIAG_OK;
   const size_t vbytes = sizeof(unsigned) * (size_t)((px - 1) * (py - 1) + 1);
   if (h->vcount_bytes < vbytes) {
@@ -242,9 +263,52 @@ ndiag_status run_edges(Handle* h, int mode, double omega, const void* w, void* z
     ND_CUDA(cudaMemsetAsync(h->vcount, 0, vbytes, h->stream));
   }
   P.vcount = h->vcount;
+  return NDIAG_OK;
+}
+
+template <class T, class TC>
+ndiag_status run_edges(Handle* h, int mode, double omega, const void* w, void* z) {
+  if (mode == NDIAG_NATURAL) return NDIAG_OK;  // one subdomain: no interfaces
+  EdgeP<T, TC> P;
+  int tasks = 0;
+  ND_TRY(edge_params(h, omega, w, z, P, tasks));
+  if (tasks <= 0) return NDIAG_OK;
   ++h->launches;
   ssor_edges_kernel<T, TC><<<(tasks + 63) / 64, 64, 0, h->stream>>>(P);
   ND_CUDA(cudaGetLastError());
+  return NDIAG_OK;
+}
+
+template <class T, class TC>
+ndiag_status edges_prepare_t(BatchSweep& b, Handle* const* hs, int np, double omega, const void* const* w,
+                             void* const* z, cudaStream_t s) {
+  std::vector<EdgeP<T, TC>> ps((size_t)np);
+  std::vector<unsigned> off((size_t)np + 1, 0);
+  for (int p = 0; p < np; ++p) {
+    int tasks = 0;
+    ND_TRY(edge_params(hs[p], omega, w[p], z[p], ps[p], tasks));
+    off[p + 1] = off[p] + (unsigned)((std::max(tasks, 0) + 63) / 64);
+  }
+  const size_t pb = sizeof(EdgeP<T, TC>) * (size_t)np, ob = sizeof(unsigned) * (size_t)(np + 1);
+  if (pb > b.params_bytes) {
+    dev_free(b.params, b.params_bytes, s);
+    b.params = dev_alloc(pb, s);
+    b.params_bytes = b.params ? pb : 0;
+  }
+  if (ob > b.off_bytes) {
+    dev_free(b.off, b.off_bytes, s);
+    b.off = (unsigned*)dev_alloc(ob, s);
+    b.off_bytes = b.off ? ob : 0;
+  }
+  if (!b.params || !b.off) return NDIAG_ENOMEM;
+  b.host_params.resize(pb);
+  std::memcpy(b.host_params.data(), ps.data(), pb);
+  b.host_off = off;
+  ND_CUDA(cudaMemcpyAsync(b.params, b.host_params.data(), pb, cudaMemcpyHostToDevice, s));
+  ND_CUDA(cudaMemcpyAsync(b.off, b.host_off.data(), ob, cudaMemcpyHostToDevice, s));
+  b.np = np;
+  b.total = off[np];
+  b.precision = hs[0]->precision;
   return NDIAG_OK;
 }
 
@@ -268,6 +332,27 @@ ndiag_status build_scaled_transposed(Handle* h, ScaledSet& set) {
     transposed_set_kernel<float><<<grid, 256, 0, h->stream>>>(nx, ny, nz, h->stencil, h->N, h->A64, (float*)set.base);
   else
     transposed_set_kernel<__half><<<grid, 256, 0, h->stream>>>(nx, ny, nz, h->stencil, h->N, h->A64, (__half*)set.base);
+  ND_CUDA(cudaGetLastError());
+  return NDIAG_OK;
+}
+
+ndiag_status batch_edges_prepare(BatchSweep& b, Handle* const* hs, int np, double omega, const void* const* w,
+                                 void* const* z, cudaStream_t s) {
+  if (np < 1) return NDIAG_EINVAL;
+  switch (hs[0]->precision) {
+    case NDIAG_FP64: return edges_prepare_t<double, double>(b, hs, np, omega, w, z, s);
+    case NDIAG_FP32: return edges_prepare_t<float, float>(b, hs, np, omega, w, z, s);
+  }
+  return NDIAG_EINVAL;
+}
+
+ndiag_status batch_edges_launch(const BatchSweep& b, cudaStream_t s) {
+  if (b.total == 0) return NDIAG_OK;
+  if (b.precision == NDIAG_FP64)
+    ssor_edges_batch_kernel<double, double><<<b.total, 64, 0, s>>>((const EdgeP<double, double>*)b.params, b.off,
+                                                                     b.np);
+  else
+    ssor_edges_batch_kernel<float, float><<<b.total, 64, 0, s>>>((const EdgeP<float, float>*)b.params, b.off, b.np);
   ND_CUDA(cudaGetLastError());
   return NDIAG_OK;
 }

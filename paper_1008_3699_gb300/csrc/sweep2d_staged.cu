@@ -44,6 +44,9 @@
 //   The edge chain keeps a group's values in registers and stores them after
 //   the group, so no memory operation sits between two positions of its
 //   recurrence. Every wait is bounded (NDIAG_ETIMEOUT).
+#include <cstring>
+#include <vector>
+
 #include "sweep_common.cuh"
 
 namespace nd {
@@ -630,8 +633,9 @@ __device__ __forceinline__ void band_run(const StagedP<T, TC>& P, const Geo& g, 
   }
 }
 
+// One slab (CTA) of one sweep; `block` numbers the slabs of the sweep.
 template <class T, class TC, int KIND, bool OM1>
-__global__ void __launch_bounds__((NW + 2) * 32, 2) sweep2d_staged_kernel(StagedP<T, TC> P) {
+__device__ __forceinline__ void staged_body(const StagedP<T, TC>& P, unsigned block) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ T inring[NW][RING];  // band w's south input: the row below its first row
   __shared__ T colval[SLAB];      // start-column values of the slab's band rows
@@ -655,7 +659,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, 2) sweep2d_staged_kernel(Staged
     if (P.use_ticket) s_ticket = atomicAdd(P.ticket, 1u);
   }
   __syncthreads();
-  const unsigned slab_id = P.use_ticket ? s_ticket : blockIdx.x;
+  const unsigned slab_id = P.use_ticket ? s_ticket : block;
   const unsigned sub = slab_id / P.spp;
   const int j = (int)(slab_id % P.spp);
   const int ix = (int)(sub % (unsigned)P.sx.p), iy = (int)(sub / (unsigned)P.sx.p);
@@ -697,6 +701,25 @@ __global__ void __launch_bounds__((NW + 2) * 32, 2) sweep2d_staged_kernel(Staged
     band_run<-1, T, TC, KIND, OM1>(P, g, rg, tx, ty, j, slab_g, warp, lane, sh);
   else
     band_run<1, T, TC, KIND, OM1>(P, g, rg, tx, ty, j, slab_g, warp, lane, sh);
+}
+
+template <class T, class TC, int KIND, bool OM1>
+__global__ void __launch_bounds__((NW + 2) * 32, 2) sweep2d_staged_kernel(StagedP<T, TC> P) {
+  staged_body<T, TC, KIND, OM1>(P, blockIdx.x);
+}
+
+// Several independent sweeps (one per problem of a batch) in one launch:
+// problem p owns blocks off[p] .. off[p+1] - 1.
+template <class T, class TC, int KIND, bool OM1>
+__global__ void __launch_bounds__((NW + 2) * 32, 2)
+    sweep2d_staged_batch_kernel(const StagedP<T, TC>* __restrict__ Pa, const unsigned* __restrict__ off, int np) {
+  int lo = 0, hi = np - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  staged_body<T, TC, KIND, OM1>(Pa[lo], blockIdx.x - off[lo]);
 }
 
 // Line table of one phase: one thread per start-row position (iy, gx) and per
@@ -836,9 +859,10 @@ ndiag_status line_table(Handle* h, const ScaledSet& set, StagedP<T, TC>& P, bool
 }
 
 template <class T, class TC>
-ndiag_status fill(Handle* h, int kind, int mode, int64_t t, const double* omega, const ScaledSet& set,
-                  const void* rhs, const void* xold, void* xnew, double beta_scale, bool rev) {
-  StagedP<T, TC> P{};
+ndiag_status make_params(Handle* h, int mode, int64_t t, const double* omega, const ScaledSet& set,
+                         const void* rhs, const void* xold, void* xnew, double beta_scale, bool rev,
+                         StagedP<T, TC>& P, unsigned& nslabs, bool& om1_out) {
+  P = StagedP<T, TC>{};
   P.nx = (int)h->n[0];
   P.ny = (int)h->n[1];
   const bool nat = mode == NDIAG_NATURAL || mode == MODE_NATURAL_REV;
@@ -870,7 +894,7 @@ ndiag_status fill(Handle* h, int kind, int mode, int64_t t, const double* omega,
   P.bscale = (T)beta_scale;
   if (beta_scale != 1.0) om1 = false;
   if (P.coupled) ND_TRY(line_table(h, set, P, om1_g, om_used));
-  const unsigned nslabs = (unsigned)(px * py * P.spp);
+  nslabs = (unsigned)(px * py * P.spp);
   if (P.use_ticket) {
     const size_t need = sizeof(unsigned) * (1 + 2 * (size_t)nslabs);
     const size_t need_ch = sizeof(T) * 2 * (size_t)nslabs;
@@ -892,6 +916,17 @@ ndiag_status fill(Handle* h, int kind, int mode, int64_t t, const double* omega,
     P.chain = (T*)h->twin_hand;
   }
   P.st = h->status;
+  om1_out = om1;
+  return NDIAG_OK;
+}
+
+template <class T, class TC>
+ndiag_status fill(Handle* h, int kind, int mode, int64_t t, const double* omega, const ScaledSet& set,
+                  const void* rhs, const void* xold, void* xnew, double beta_scale, bool rev) {
+  StagedP<T, TC> P;
+  unsigned nslabs = 0;
+  bool om1 = true;
+  ND_TRY(make_params(h, mode, t, omega, set, rhs, xold, xnew, beta_scale, rev, P, nslabs, om1));
   if (kind == KIND_SOR)
     return om1 ? launch<T, TC, KIND_SOR, true>(h, P, nslabs) : launch<T, TC, KIND_SOR, false>(h, P, nslabs);
   if (kind == KIND_TRI_SCALED)
@@ -903,7 +938,114 @@ ndiag_status fill(Handle* h, int kind, int mode, int64_t t, const double* omega,
   return NDIAG_EINVAL;
 }
 
+
+template <class T, class TC, int KIND, bool OM1>
+ndiag_status launch_batch(const BatchSweep& b, cudaStream_t s) {
+  using C = Cfg<T, TC, KIND>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    ND_CUDA(cudaFuncSetAttribute(sweep2d_staged_batch_kernel<T, TC, KIND, OM1>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES));
+    attr_set = true;
+  }
+  sweep2d_staged_batch_kernel<T, TC, KIND, OM1><<<b.total, (NW + 2) * 32, C::BYTES, s>>>(
+      (const StagedP<T, TC>*)b.params, b.off, b.np);
+  ND_CUDA(cudaGetLastError());
+  return NDIAG_OK;
+}
+
+template <class T, class TC>
+ndiag_status batch_prepare_t(BatchSweep& b, Handle* const* hs, int np, int kind, int mode, int64_t t,
+                             const double* omega, int set_sel, const void* const* rhs, const void* const* xold,
+                             void* const* xnew, double beta_scale, bool rev, cudaStream_t s) {
+  std::vector<StagedP<T, TC>> ps((size_t)np);
+  std::vector<unsigned> off((size_t)np + 1, 0);
+  bool om1_all = true;
+  for (int p = 0; p < np; ++p) {
+    Handle* h = hs[p];
+    const ScaledSet& set = set_sel == 0 ? h->sor : (set_sel == 1 ? h->ilu : h->sorT);
+    unsigned ns = 0;
+    bool om1 = true;
+    ND_TRY(make_params(h, mode, t, omega, set, rhs[p], xold ? xold[p] : nullptr, xnew[p], beta_scale, rev, ps[p],
+                       ns, om1));
+    if (ps[p].use_ticket) {
+      set_error("batched sweeps need subdomains of at most 128 rows");
+      return NDIAG_EINVAL;
+    }
+    if (p == 0) om1_all = om1;
+    if (om1 != om1_all) return NDIAG_EINVAL;
+    off[p + 1] = off[p] + ns;
+  }
+  const size_t pb = sizeof(StagedP<T, TC>) * (size_t)np, ob = sizeof(unsigned) * (size_t)(np + 1);
+  if (pb > b.params_bytes) {
+    dev_free(b.params, b.params_bytes, s);
+    b.params = dev_alloc(pb, s);
+    b.params_bytes = b.params ? pb : 0;
+  }
+  if (ob > b.off_bytes) {
+    dev_free(b.off, b.off_bytes, s);
+    b.off = (unsigned*)dev_alloc(ob, s);
+    b.off_bytes = b.off ? ob : 0;
+  }
+  if (!b.params || !b.off) return NDIAG_ENOMEM;
+  b.host_params.resize(pb);
+  std::memcpy(b.host_params.data(), ps.data(), pb);
+  b.host_off = off;
+  ND_CUDA(cudaMemcpyAsync(b.params, b.host_params.data(), pb, cudaMemcpyHostToDevice, s));
+  ND_CUDA(cudaMemcpyAsync(b.off, b.host_off.data(), ob, cudaMemcpyHostToDevice, s));
+  b.np = np;
+  b.total = off[np];
+  b.kind = kind;
+  b.om1 = om1_all;
+  b.precision = hs[0]->precision;
+  double bytes = 0.0;
+  for (int p = 0; p < np; ++p) {
+    const int64_t N = hs[p]->N;
+    bytes += kind == KIND_SOR ? staged_bytes<T, TC, KIND_SOR>(N)
+                              : (kind == KIND_TRI_SCALED ? staged_bytes<T, TC, KIND_TRI_SCALED>(N)
+                                                         : staged_bytes<T, TC, KIND_TRI_UNIT>(N));
+  }
+  b.bytes = bytes;
+  return NDIAG_OK;
+}
+
+template <class T, class TC>
+ndiag_status batch_launch_t(const BatchSweep& b, cudaStream_t s) {
+  if (b.kind == KIND_SOR) return b.om1 ? launch_batch<T, TC, KIND_SOR, true>(b, s) : launch_batch<T, TC, KIND_SOR, false>(b, s);
+  if (b.kind == KIND_TRI_SCALED)
+    return b.om1 ? launch_batch<T, TC, KIND_TRI_SCALED, true>(b, s) : launch_batch<T, TC, KIND_TRI_SCALED, false>(b, s);
+  return b.om1 ? launch_batch<T, TC, KIND_TRI_UNIT, true>(b, s) : launch_batch<T, TC, KIND_TRI_UNIT, false>(b, s);
+}
+
 }  // namespace
+
+ndiag_status batch_sweep_prepare(BatchSweep& b, Handle* const* hs, int np, int kind, int mode, int64_t t,
+                                 const double* omega, int set_sel, const void* const* rhs, const void* const* xold,
+                                 void* const* xnew, double beta_scale, bool rev, cudaStream_t s) {
+  if (np < 1) return NDIAG_EINVAL;
+  for (int p = 0; p < np; ++p)
+    if (hs[p]->dim != 2 || hs[p]->stencil != 5 || hs[p]->precision != hs[0]->precision) return NDIAG_EINVAL;
+  switch (hs[0]->precision) {
+    case NDIAG_FP64:
+      return batch_prepare_t<double, double>(b, hs, np, kind, mode, t, omega, set_sel, rhs, xold, xnew, beta_scale,
+                                             rev, s);
+    case NDIAG_FP32:
+      return batch_prepare_t<float, float>(b, hs, np, kind, mode, t, omega, set_sel, rhs, xold, xnew, beta_scale,
+                                           rev, s);
+  }
+  return NDIAG_EINVAL;
+}
+
+ndiag_status batch_sweep_launch(const BatchSweep& b, cudaStream_t s) {
+  if (b.total == 0) return NDIAG_OK;
+  return b.precision == NDIAG_FP64 ? batch_launch_t<double, double>(b, s) : batch_launch_t<float, float>(b, s);
+}
+
+void batch_sweep_free(BatchSweep& b, cudaStream_t s) {
+  dev_free(b.params, b.params_bytes, s);
+  dev_free(b.off, b.off_bytes, s);
+  b = BatchSweep{};
+}
 
 // Returns NDIAG_EINVAL when this kernel does not cover the request (the
 // caller then uses the single-pass kernel).

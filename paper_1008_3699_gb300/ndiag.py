@@ -27,7 +27,9 @@ PREC_NONE, PREC_SSOR, PREC_ILU0 = 0, 1, 2
 # every symbol include/ndiag.h declares
 EXPORTED = ["ndiag_set_allocator", "ndiag_last_error", "ndiag_create", "ndiag_destroy", "ndiag_cells",
             "ndiag_precision", "sor_sweep", "ssor_apply", "ilu0_factor", "ilu0_apply", "ndiag_residual",
-            "krylov_solve", "ndiag_profile", "ndiag_read_counters", "ilu0_apply_noalloc"]
+            "krylov_solve", "ndiag_profile", "ndiag_read_counters", "ilu0_apply_noalloc",
+            "ndiag_batch_create", "ndiag_batch_autotune", "ndiag_batch_tiles", "ndiag_batch_solve",
+            "ndiag_batch_cells", "ndiag_batch_launches", "ndiag_batch_destroy"]
 NOALLOC_MAX_CELLS = 1 << 20
 
 
@@ -81,6 +83,16 @@ def load(path: str = LIB_PATH):
     L.krylov_solve.argtypes = [P, I, I, I, P, D, I, P, P, ctypes.POINTER(SolveInfo)]
     L.ndiag_profile.argtypes = [P, I]
     L.ndiag_read_counters.argtypes = [P, ctypes.POINTER(Counters)]
+    L.ndiag_batch_create.argtypes = [ctypes.POINTER(P), I, P, P, P, P, D, P]
+    L.ndiag_batch_autotune.argtypes = [P, P]
+    L.ndiag_batch_tiles.argtypes = [P, P]
+    L.ndiag_batch_solve.argtypes = [P, D, I, P, P, P]
+    L.ndiag_batch_cells.argtypes = [P]
+    L.ndiag_batch_cells.restype = L64
+    L.ndiag_batch_launches.argtypes = [P]
+    L.ndiag_batch_launches.restype = L64
+    L.ndiag_batch_destroy.argtypes = [P]
+    L.ndiag_batch_destroy.restype = None
     if path == LIB_PATH:
         _lib = L
     return L
@@ -207,3 +219,63 @@ class NDiag:
             _check(self.L, st)
         return dict(iters=info.iterations, outer=info.outer, relres=info.relres, seconds=info.seconds,
                     status=STATUS_NAMES[st])
+
+
+class Batch:
+    """Many independent 2D 5-point problems solved together (fp32 SSOR-PCG with
+    fp64 refinement). problems: list of dicts with n=(nx, ny, 1) and diags
+    (5 x nx*ny); vectors are concatenated in problem order."""
+
+    def __init__(self, problems, tile=None, omega=1.0, stream=None):
+        import torch
+        self.L = load()
+        _install_torch_allocator(self.L)
+        self.count = len(problems)
+        nx = np.array([int(p["n"][0]) for p in problems], dtype=np.int64)
+        ny = np.array([int(p["n"][1]) for p in problems], dtype=np.int64)
+        self._diags = [np.ascontiguousarray(p["diags"], dtype=np.float64) for p in problems]
+        ptrs = (ctypes.c_void_p * self.count)(*[d.ctypes.data for d in self._diags])
+        tl = None if tile is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(tile, dtype=np.int32), (self.count,)))
+        self.offsets = np.concatenate([[0], np.cumsum(nx * ny)]).astype(np.int64)
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        h = ctypes.c_void_p()
+        _check(self.L, self.L.ndiag_batch_create(ctypes.byref(h), self.count, _ptr(nx), _ptr(ny), ptrs,
+                                                 _ptr(tl), float(omega), ctypes.c_void_p(s)))
+        self.h = h
+
+    @property
+    def cells(self):
+        return int(self.L.ndiag_batch_cells(self.h))
+
+    def launches(self):
+        return int(self.L.ndiag_batch_launches(self.h))
+
+    def autotune(self, b):
+        _check(self.L, self.L.ndiag_batch_autotune(self.h, _ptr(b)))
+
+    def tiles(self):
+        t = np.zeros(self.count, dtype=np.int32)
+        _check(self.L, self.L.ndiag_batch_tiles(self.h, _ptr(t)))
+        return t
+
+    def solve(self, b, x, rtol=1e-8, maxit=20000, raise_on_noconv=True):
+        """b, x: concatenated fp64 CUDA tensors; x is updated. Returns per-problem infos."""
+        infos = (SolveInfo * self.count)()
+        st = self.L.ndiag_batch_solve(self.h, float(rtol), int(maxit), _ptr(b), _ptr(x), infos)
+        if st != OK and (raise_on_noconv or st != ENOCONV):
+            _check(self.L, st)
+        return [dict(iters=i.iterations, outer=i.outer, relres=i.relres, seconds=i.seconds,
+                     status=STATUS_NAMES[i.status] if 0 <= i.status < len(STATUS_NAMES) else str(i.status))
+                for i in infos]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ndiag_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
