@@ -194,6 +194,10 @@ ndiag_status do_ilu_apply(Handle* h, const void* r, void* z) {
     ND_TRY(launch_sweep3d(h, KIND_TRI_SCALED, h->ilu_mode, tf, nullptr, h->ilu, r, nullptr, h->tmp, 1.0, false));
     return launch_sweep3d(h, KIND_TRI_UNIT, back, tf ^ 1, nullptr, h->ilu, h->tmp, nullptr, z, 1.0, false);
   }
+  if (h->stencil == 9) {
+    ND_TRY(launch_sweep9(h, KIND_TRI_SCALED, h->ilu_mode, tf, nullptr, h->ilu, r, nullptr, h->tmp, 1.0));
+    return launch_sweep9(h, KIND_TRI_UNIT, back, tf ^ 1, nullptr, h->ilu, h->tmp, nullptr, z, 1.0);
+  }
   ND_TRY(launch_sweep2d(h, KIND_TRI_SCALED, h->ilu_mode, tf, nullptr, h->ilu, r, nullptr, h->tmp));
   ND_TRY(launch_sweep2d(h, KIND_TRI_UNIT, back, tf ^ 1, nullptr, h->ilu, h->tmp, nullptr, z));
   return NDIAG_OK;
@@ -205,6 +209,10 @@ ndiag_status check_device_status(Handle* h) { return check_status(h); }
 ndiag_status do_ssor_apply(Handle* h, int mode, double omega, const void* r, void* z) {
   if (!(omega > 0.0 && omega < 2.0)) {
     set_error("SSOR needs 0 < omega < 2");
+    return NDIAG_EINVAL;
+  }
+  if (h->stencil == 9) {
+    set_error("SSOR is not available for the 9-point stencil (use SOR or ILU(0))");
     return NDIAG_EINVAL;
   }
   ND_TRY(ensure_tmp(h));
@@ -270,10 +278,7 @@ ndiag_status ndiag_create(ndiag** out, int dim, const int64_t n[3], int stencil,
       set_error("diagonal entries must be positive");
       return NDIAG_EINVAL;
     }
-  if (stencil == 9) {
-    set_error("stencil not supported by this build yet");
-    return NDIAG_EINVAL;
-  }
+
   ndiag* h = new (std::nothrow) ndiag();
   if (!h) return NDIAG_ENOMEM;
   h->dim = dim;
@@ -394,6 +399,7 @@ ndiag_status sor_sweep(ndiag* h, int mode, const double* omega, int64_t t, const
   if (!h || !omega || !b || !x_old || !x_new || x_old == x_new) return NDIAG_EINVAL;
   if (mode != NDIAG_NATURAL && mode != NDIAG_DECOMPOSED) return NDIAG_EINVAL;
   if (h->dim == 3) return launch_sweep3d(h, KIND_SOR, mode, t, omega, h->sor, b, x_old, x_new, 1.0, false);
+  if (h->stencil == 9) return launch_sweep9(h, KIND_SOR, mode, t, omega, h->sor, b, x_old, x_new, 1.0);
   return launch_sweep2d(h, KIND_SOR, mode, t, omega, h->sor, b, x_old, x_new);
 }
 
@@ -401,8 +407,14 @@ ndiag_status ilu0_factor(ndiag* h, int mode) {
   if (!h || (mode != NDIAG_NATURAL && mode != NDIAG_DECOMPOSED)) return NDIAG_EINVAL;
   double* dt = (double*)dev_alloc(sizeof(double) * (size_t)h->N, h->stream);
   if (!dt) return NDIAG_ENOMEM;
-  ndiag_status st =
-      h->dim == 3 ? launch_ilu_factor3d_into(h, mode, dt) : launch_ilu_factor2d_into(h, mode, dt);
+  if (h->stencil == 9 && mode == NDIAG_NATURAL) {
+    dev_free(dt, sizeof(double) * (size_t)h->N, h->stream);
+    set_error("natural-order ILU(0) of the 9-point stencil is not available (decomposed D-ILU is)");
+    return NDIAG_EINVAL;
+  }
+  ndiag_status st = h->dim == 3        ? launch_ilu_factor3d_into(h, mode, dt)
+                    : h->stencil == 9 ? launch_ilu_factor9_into(h, mode, dt)
+                                      : launch_ilu_factor2d_into(h, mode, dt);
   if (st == NDIAG_OK) st = build_scaled(h, h->ilu, dt);
   dev_free(dt, sizeof(double) * (size_t)h->N, h->stream);
   if (st == NDIAG_OK) st = check_status(h);

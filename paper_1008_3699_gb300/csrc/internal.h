@@ -199,6 +199,10 @@ void handle_set_sub(Handle* h, const int sub[3]);
 ndiag_status launch_sweep3d(Handle* h, int kind, int mode, int64_t t, const double* omega, const ScaledSet& set,
                             const void* rhs, const void* xold, void* xnew, double beta_scale, bool transposed);
 ndiag_status launch_ilu_factor3d_into(Handle* h, int mode, double* out);
+// 2D 9-point sweeps by levels (sweep9.cu); D-ILU pivots of the decomposed 9-point factor
+ndiag_status launch_sweep9(Handle* h, int kind, int mode, int64_t t, const double* omega, const ScaledSet& set,
+                           const void* rhs, const void* xold, void* xnew, double beta_scale);
+ndiag_status launch_ilu_factor9_into(Handle* h, int mode, double* out);
 ndiag_status build_scaled_transposed(Handle* h, ScaledSet& set);
 
 // BLAS-1 and SpMV (blas.cu)

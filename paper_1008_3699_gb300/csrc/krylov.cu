@@ -226,6 +226,8 @@ ndiag_status stationary(Handle* h, int mode, const double* omega, const T* b, T*
   while (rel > tol_abs && it < maxit) {
     if (h->dim == 3)
       ND_TRY(launch_sweep3d(h, KIND_SOR, mode, it, omega, h->sor, b, cur, nxt, 1.0, false));
+    else if (h->stencil == 9)
+      ND_TRY(launch_sweep9(h, KIND_SOR, mode, it, omega, h->sor, b, cur, nxt, 1.0));
     else
       ND_TRY(launch_sweep2d(h, KIND_SOR, mode, it, omega, h->sor, b, cur, nxt));
     ++it;

@@ -1,0 +1,364 @@
+// Decomposed sequential sweep on 2D 9-point matrices (sm_103a), by levels.
+//
+// The paper calls the 9-point extension straightforward and gives no detail
+// (Sec. 3). This library reads it as: inside a subdomain the cells are taken
+// in lexicographic order of the reflected frame, so the new values of a cell
+// are its W, SW, S and SE neighbours; across an interface only face
+// neighbours couple, and only when both subdomains start at the interface
+// (mutual, solved together as in Eqs. 2d:sor2b2 and 2d:sor4b4); diagonal
+// neighbours across an interface keep their old values. With one subdomain
+// this is natural-order SOR on the 9-point molecule.
+//
+// Level of own cell (x, y): x + 2y (SE = (x+1, y-1) then sits one level
+// lower). One CTA per subdomain walks the levels; the block of a cell on a
+// coupled start line holds its twins (2 or 4 cells, canonical order). An
+// x-twin's SE neighbour is one column inside the neighbouring subdomain, so
+// the two CTAs of an x-interface advance in step: before level L a CTA waits
+// (bounded) until its x-neighbour has published level L - 1. All CTAs of the
+// launch must be resident at once; the launcher checks that.
+#include "sweep_common.cuh"
+
+namespace nd {
+namespace {
+
+using namespace sweep;
+
+constexpr int T9 = 256;
+
+template <class T, class TC>
+struct P9 {
+  int nx, ny;
+  Split sx, sy;
+  int base, coupled;
+  const TC* inv;
+  const TC* c[8];  // scaled entries W E S N SW SE NW NE
+  const T* rhs;
+  const T* xold;
+  T* xnew;
+  T om[4];
+  T bscale;
+  unsigned* prog;  // per subdomain: levels completed (zeroed before the launch)
+  DevStatus* st;
+};
+
+// entry of the neighbour at local offset (dx, dy) for corner bits (cx, cy)
+__device__ __forceinline__ int ent9(int dx, int dy, int cx, int cy) {
+  const int gx = cx ? -dx : dx, gy = cy ? -dy : dy;
+  if (gy == 0) return gx < 0 ? 0 : 1;
+  if (gx == 0) return gy < 0 ? 2 : 3;
+  if (gy < 0) return gx < 0 ? 4 : 5;
+  return gx < 0 ? 6 : 7;
+}
+
+struct Sub9 {
+  int ix, iy, g0[2], len[2], c[2], t[2];
+  __device__ int gco(int a, int l) const { return c[a] ? g0[a] + len[a] - 1 - l : g0[a] + l; }
+};
+
+template <class T, class TC>
+__device__ __forceinline__ Sub9 sub9(const P9<T, TC>& P, int ix, int iy) {
+  Sub9 S;
+  S.ix = ix;
+  S.iy = iy;
+  S.g0[0] = P.sx.lo(ix);
+  S.len[0] = P.sx.len(ix);
+  S.g0[1] = P.sy.lo(iy);
+  S.len[1] = P.sy.len(iy);
+  const int cidx = P.base ^ (ix & 1) ^ ((iy & 1) << 1);
+  S.c[0] = cidx & 1;
+  S.c[1] = (cidx >> 1) & 1;
+  S.t[0] = P.coupled && (S.c[0] ? S.g0[0] + S.len[0] < P.nx : S.g0[0] > 0);
+  S.t[1] = P.coupled && (S.c[1] ? S.g0[1] + S.len[1] < P.ny : S.g0[1] > 0);
+  return S;
+}
+
+// Twin store: x-twins (-1, y) at [y], y-twins (x, -1) at [h + x], corner at [h + w].
+__device__ __forceinline__ int slot9(int sub, const int* lc, int w, int h) {
+  return sub == 1 ? lc[1] : (sub == 2 ? h + lc[0] : h + w);
+}
+
+template <class T, class TC, int KIND, bool OM1>
+__global__ void __launch_bounds__(T9) sweep9_kernel(P9<T, TC> P) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  T* tw = reinterpret_cast<T*>(gsm);
+  const int ix = (int)(blockIdx.x % (unsigned)P.sx.p), iy = (int)(blockIdx.x / (unsigned)P.sx.p);
+  const Sub9 S = sub9(P, ix, iy);
+  const int w = S.len[0], h = S.len[1];
+  const int lmax = (w - 1) + 2 * (h - 1);
+  const int tcode = S.t[0] | (S.t[1] << 1);
+  // x-neighbour across the coupled start line (its interior feeds the x-twins)
+  const int nbx = S.c[0] ? ix + 1 : ix - 1;
+  const unsigned* nprog = S.t[0] ? P.prog + (iy * P.sx.p + nbx) : nullptr;
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) s_ok = 1;
+  __syncthreads();
+  for (int L = 0; L <= lmax; ++L) {
+    if (nprog && L >= 2 && (L & 1) == 0 && L / 2 < h) {  // x-face block at this level
+      if (threadIdx.x == 0 && s_ok) s_ok = wait_gmem(nprog, (unsigned)L, P.st) ? 1 : 0;
+      __syncthreads();
+      if (!s_ok) return;
+    }
+    for (int y = threadIdx.x; y < h; y += T9) {
+      const int x = L - 2 * y;
+      if (x < 0 || x >= w) continue;
+      const int own[2] = {x, y};
+      const int C = ((x == 0) | ((y == 0) << 1)) & tcode;
+      int axes[2], nC = 0;
+      for (int a = 0; a < 2; ++a)
+        if (C >> a & 1) axes[nC++] = a;
+      const int n = 1 << nC;
+      int mo = 0;
+      for (int r = 0; r < nC; ++r)
+        if (S.c[axes[r]] == 0) mo |= 1 << r;
+      T M[4][4], hv[4];
+      int64_t gidx[4];
+      for (int m = 0; m < n; ++m) {
+        int lc[2] = {own[0], own[1]}, sub = 0;
+        for (int r = 0; r < nC; ++r)
+          if (((m ^ mo) >> r) & 1) {
+            lc[axes[r]] = -1;
+            sub |= 1 << axes[r];
+          }
+        const int cm0 = S.c[0] ^ (sub & 1), cm1 = S.c[1] ^ ((sub >> 1) & 1);
+        // extent of the member's subdomain and its local coordinates there
+        int mlen[2], ml[2];
+        for (int a = 0; a < 2; ++a) {
+          if ((sub >> a) & 1) {
+            const int ia = a == 0 ? (S.c[0] ? S.ix + 1 : S.ix - 1) : (S.c[1] ? S.iy + 1 : S.iy - 1);
+            mlen[a] = a == 0 ? P.sx.len(ia) : P.sy.len(ia);
+            ml[a] = 0;
+          } else {
+            mlen[a] = S.len[a];
+            ml[a] = lc[a];
+          }
+        }
+        const int gx = S.gco(0, lc[0]), gy = S.gco(1, lc[1]);
+        const int64_t gi = (int64_t)gy * P.nx + gx;
+        gidx[m] = gi;
+        const T om = OM1 ? T(1) : P.om[cm0 | (cm1 << 1)];
+        for (int k = 0; k < n; ++k) M[m][k] = T(0);
+        M[m][m] = T(1);
+        // explicit part (old values; SOR only) and the implicit part, each in
+        // the member's own neighbour order, so every CTA forms the same terms
+        T base = (KIND == KIND_TRI_UNIT) ? __ldg(P.rhs + gi) : ldco<T, TC>(P.inv + gi) * __ldg(P.rhs + gi);
+        T impl = T(0);
+        const int offs[8][2] = {{-1, 0}, {-1, -1}, {0, -1}, {1, -1}, {1, 0}, {1, 1}, {0, 1}, {-1, 1}};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int dx = offs[q][0], dy = offs[q][1];
+          const int qx = ml[0] + dx, qy = ml[1] + dy;
+          const int e = ent9(dx, dy, cm0, cm1);
+          const int ggx = gx + (cm0 ? -dx : dx), ggy = gy + (cm1 ? -dy : dy);
+          if (ggx < 0 || ggx >= P.nx || ggy < 0 || ggy >= P.ny) continue;
+          const bool upstream = q < 4;  // W, SW, S, SE
+          const bool inside = qx >= 0 && qx < mlen[0] && qy >= 0 && qy < mlen[1];
+          const int64_t gq = (int64_t)ggy * P.nx + ggx;
+          if (upstream && inside) {
+            // new value of a cell of the member's own subdomain
+            T g = ldco<T, TC>(P.c[e] + gi);
+            if (!OM1) g *= om;
+            T v;
+            if (sub == 0) {
+              v = __ldcg(P.xnew + gq);
+            } else {
+              // in S-coordinates: still on the twin line -> shared store, deeper -> global
+              const int nl[2] = {lc[0] + (cm0 == S.c[0] ? dx : -dx), lc[1] + (cm1 == S.c[1] ? dy : -dy)};
+              const bool on_line = ((sub & 1) ? nl[0] == -1 : nl[0] >= 0) && ((sub & 2) ? nl[1] == -1 : nl[1] >= 0);
+              v = on_line ? tw[slot9(sub, nl, w, h)] : __ldcg(P.xnew + gq);
+            }
+            impl = fma(g, v, impl);
+          } else if (upstream && (dx == 0 || dy == 0) && ((C >> (dx != 0 ? 0 : 1)) & 1)) {
+            // face neighbour across a coupled start line: the block partner
+            const int a = dx != 0 ? 0 : 1;
+            int r = 0;
+            while (axes[r] != a) ++r;
+            T g = ldco<T, TC>(P.c[e] + gi);
+            if (!OM1) g *= om;
+            M[m][m ^ (1 << r)] = g;
+          } else if (KIND == KIND_SOR) {
+            // downstream neighbours, uncoupled or diagonal ones across an interface: old values
+            base = fma(-ldco<T, TC>(P.c[e] + gi), __ldg(P.xold + gq), base);
+          }
+        }
+        T acc;
+        if (KIND == KIND_SOR) acc = OM1 ? base : fma(om, base, (T(1) - om) * __ldg(P.xold + gi));
+        else if (KIND == KIND_TRI_SCALED) acc = OM1 ? base : P.bscale * base;
+        else acc = base;
+        acc -= impl;
+        hv[m] = acc;
+      }
+      for (int k = 0; k < n; ++k) {
+        const T piv = M[k][k];
+        for (int i = k + 1; i < n; ++i) {
+          const T f = M[i][k] / piv;
+          if (f != T(0)) {
+            for (int j = k + 1; j < n; ++j) M[i][j] = fma(-f, M[k][j], M[i][j]);
+            hv[i] = fma(-f, hv[k], hv[i]);
+          }
+        }
+      }
+      T xs[4];
+      for (int k = n - 1; k >= 0; --k) {
+        T s = hv[k];
+        for (int j = k + 1; j < n; ++j) s = fma(-M[k][j], xs[j], s);
+        xs[k] = s / M[k][k];
+      }
+      for (int m = 0; m < n; ++m) {
+        if (m == mo) {
+          P.xnew[gidx[m]] = xs[m];
+        } else {
+          int lc[2] = {own[0], own[1]}, sub = 0;
+          for (int r = 0; r < nC; ++r)
+            if (((m ^ mo) >> r) & 1) {
+              lc[axes[r]] = -1;
+              sub |= 1 << axes[r];
+            }
+          tw[slot9(sub, lc, w, h)] = xs[m];
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && P.coupled) {
+      __threadfence();
+      st_release(P.prog + blockIdx.x, (unsigned)(L + 1));
+    }
+  }
+}
+
+// D-ILU pivots of the 9-point matrix: d_i = a_ii - sum over the implicit
+// upstream cells j of the same subdomain (W, SW, S, SE) of a_ij a_ji / d_j.
+__global__ void __launch_bounds__(T9) factor9_kernel(P9<double, double> P, const double* A, double* piv, int64_t N) {
+  const int ix = (int)(blockIdx.x % (unsigned)P.sx.p), iy = (int)(blockIdx.x / (unsigned)P.sx.p);
+  const Sub9 S = sub9(P, ix, iy);
+  const int w = S.len[0], h = S.len[1];
+  const int lmax = (w - 1) + 2 * (h - 1);
+  const int offs[4][2] = {{-1, 0}, {-1, -1}, {0, -1}, {1, -1}};
+  for (int L = 0; L <= lmax; ++L) {
+    for (int y = threadIdx.x; y < h; y += T9) {
+      const int x = L - 2 * y;
+      if (x < 0 || x >= w) continue;
+      const int gx = S.gco(0, x), gy = S.gco(1, y);
+      const int64_t gi = (int64_t)gy * P.nx + gx;
+      double di = A[gi];
+      for (int q = 0; q < 4; ++q) {
+        const int qx = x + offs[q][0], qy = y + offs[q][1];
+        if (qx < 0 || qx >= w || qy < 0 || qy >= h) continue;
+        const int e = ent9(offs[q][0], offs[q][1], S.c[0], S.c[1]);
+        const int eb = ent9(-offs[q][0], -offs[q][1], S.c[0], S.c[1]);
+        const int64_t gq = (int64_t)S.gco(1, qy) * P.nx + S.gco(0, qx);
+        di -= A[(size_t)(1 + e) * N + gi] * A[(size_t)(1 + eb) * N + gq] / __ldcg(piv + gq);
+      }
+      if (di == 0.0) atomicExch(&P.st->zero_pivot, 1);
+      piv[gi] = di;
+    }
+    __syncthreads();
+  }
+}
+
+template <class T, class TC>
+P9<T, TC> params9(Handle* h, int mode, int64_t t, const ScaledSet& set, const void* rhs, const void* xold,
+                  void* xnew, unsigned& nsub) {
+  P9<T, TC> P{};
+  const bool nat = mode == NDIAG_NATURAL || mode == MODE_NATURAL_REV;
+  P.nx = (int)h->n[0];
+  P.ny = (int)h->n[1];
+  const int px = nat ? 1 : h->sub[0], py = nat ? 1 : h->sub[1];
+  P.sx = Split{px, P.nx / px, P.nx % px};
+  P.sy = Split{py, P.ny / py, P.ny % py};
+  P.base = nat ? (mode == MODE_NATURAL_REV ? 3 : 0) : base_corner(2, t);
+  P.coupled = nat ? 0 : 1;
+  const size_t N = (size_t)h->N;
+  const TC* b = (const TC*)set.base;
+  P.inv = b;
+  for (int e = 0; e < 8; ++e) P.c[e] = b + (size_t)(1 + e) * N;
+  P.rhs = (const T*)rhs;
+  P.xold = (const T*)xold;
+  P.xnew = (T*)xnew;
+  P.st = h->status;
+  nsub = (unsigned)(px * py);
+  return P;
+}
+
+template <class T, class TC, int KIND, bool OM1>
+ndiag_status run9(Handle* h, P9<T, TC>& P, unsigned nsub, double bytes) {
+  const int w = P.sx.len(0), hh = P.sy.len(0);
+  const size_t smem = sizeof(T) * (size_t)(w + hh + 1);
+  static bool attr = false;
+  if (!attr) {
+    ND_CUDA(cudaFuncSetAttribute(sweep9_kernel<T, TC, KIND, OM1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 96 * 1024));
+    attr = true;
+  }
+  if (smem > 96 * 1024) return NDIAG_EINVAL;
+  if (P.coupled) {
+    // the x-interfaces advance in step: every CTA must be resident
+    int per_sm = 0;
+    ND_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep9_kernel<T, TC, KIND, OM1>, T9, smem));
+    if ((int64_t)per_sm * h->sm_count < (int64_t)nsub) {
+      set_error("9-point decomposed sweep: more subdomains than resident CTAs");
+      return NDIAG_EINVAL;
+    }
+    const size_t need = sizeof(unsigned) * nsub;
+    if (need > h->sync_bytes) {
+      dev_free(h->sync, h->sync_bytes, h->stream);
+      h->sync = (unsigned*)dev_alloc(need, h->stream);
+      h->sync_bytes = h->sync ? need : 0;
+      if (!h->sync) return NDIAG_ENOMEM;
+    }
+    ND_CUDA(cudaMemsetAsync(h->sync, 0, need, h->stream));
+    P.prog = h->sync;
+  }
+  const int slot = prof_begin(h);
+  ++h->launches;
+  ++h->sweep_launches;
+  sweep9_kernel<T, TC, KIND, OM1><<<nsub, T9, smem, h->stream>>>(P);
+  ND_CUDA(cudaGetLastError());
+  prof_end(h, slot, bytes);
+  return NDIAG_OK;
+}
+
+template <class T, class TC>
+ndiag_status sweep9_t(Handle* h, int kind, int mode, int64_t t, const double* omega, const ScaledSet& set,
+                      const void* rhs, const void* xold, void* xnew, double beta_scale) {
+  unsigned nsub = 0;
+  P9<T, TC> P = params9<T, TC>(h, mode, t, set, rhs, xold, xnew, nsub);
+  bool om1 = beta_scale == 1.0;
+  for (int k = 0; k < 4; ++k) {
+    const double wv = omega ? (mode == NDIAG_DECOMPOSED ? omega[k] : omega[0]) : 1.0;
+    P.om[k] = (T)wv;
+    if (wv != 1.0) om1 = false;
+  }
+  P.bscale = (T)beta_scale;
+  const double cellbytes = kind == KIND_SOR ? 9.0 * sizeof(TC) + 3.0 * sizeof(T)
+                                            : (kind == KIND_TRI_SCALED ? 5.0 : 4.0) * sizeof(TC) + 2.0 * sizeof(T);
+  const double bytes = cellbytes * (double)h->N;
+  if (kind == KIND_SOR)
+    return om1 ? run9<T, TC, KIND_SOR, true>(h, P, nsub, bytes) : run9<T, TC, KIND_SOR, false>(h, P, nsub, bytes);
+  if (kind == KIND_TRI_SCALED)
+    return om1 ? run9<T, TC, KIND_TRI_SCALED, true>(h, P, nsub, bytes)
+               : run9<T, TC, KIND_TRI_SCALED, false>(h, P, nsub, bytes);
+  return om1 ? run9<T, TC, KIND_TRI_UNIT, true>(h, P, nsub, bytes)
+             : run9<T, TC, KIND_TRI_UNIT, false>(h, P, nsub, bytes);
+}
+
+}  // namespace
+
+ndiag_status launch_sweep9(Handle* h, int kind, int mode, int64_t t, const double* omega, const ScaledSet& set,
+                           const void* rhs, const void* xold, void* xnew, double beta_scale) {
+  switch (h->precision) {
+    case NDIAG_FP64: return sweep9_t<double, double>(h, kind, mode, t, omega, set, rhs, xold, xnew, beta_scale);
+    case NDIAG_FP32: return sweep9_t<float, float>(h, kind, mode, t, omega, set, rhs, xold, xnew, beta_scale);
+    default: return sweep9_t<float, __half>(h, kind, mode, t, omega, set, rhs, xold, xnew, beta_scale);
+  }
+}
+
+ndiag_status launch_ilu_factor9_into(Handle* h, int mode, double* out) {
+  unsigned nsub = 0;
+  P9<double, double> P = params9<double, double>(h, mode, fwd_phase(2), h->sor, nullptr, nullptr, nullptr, nsub);
+  ++h->launches;
+  factor9_kernel<<<nsub, T9, 0, h->stream>>>(P, h->A64, out, h->N);
+  ND_CUDA(cudaGetLastError());
+  return NDIAG_OK;
+}
+
+}  // namespace nd

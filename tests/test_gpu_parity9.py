@@ -1,0 +1,133 @@
+"""GPU parity of the 2D 9-point path (level sweep with x-interface lockstep,
+sweep9.cu) against the CPU oracle, through the C ABI: SOR sweeps of every
+phase and the natural ordering, the decomposed D-ILU factor and apply to 1e-12
+(fp64), fp32 sweeps to 2e-5, and an ILU(0)-BiCGSTAB solve of the 9-point
+convection-diffusion operator inside the oracle's iteration envelope.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1008_3699_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+CASES = [((20, 17), (2, 2)), ((33, 25), (3, 2)), ((9, 12), (9, 4)), ((40, 40), (4, 4))]
+
+
+@pytest.fixture(scope="module")
+def nd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1008_3699_gb300 import build, ndiag
+    build.build()
+    return ndiag
+
+
+def _t(a, dtype=None):
+    import torch
+    return torch.tensor(np.asarray(a), dtype=dtype or torch.float64, device="cuda")
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _rand9(n, seed):
+    g = np.random.default_rng(seed)
+    N = n[0] * n[1]
+    d = -g.uniform(0.1, 0.8, size=(9, N))
+    d = W._zero_outside(d, (n[0], n[1]), 9)
+    d[0] = -d[1:].sum(axis=0) + g.uniform(0.05, 0.5, N)
+    return d
+
+
+@pytest.mark.parametrize("n,sub", CASES)
+def test_sor_sweep9_all_phases_fp64(nd, n, sub):
+    d = _rand9(n, 91)
+    N = n[0] * n[1]
+    g = np.random.default_rng(92)
+    b, u = g.uniform(-1, 1, N), g.uniform(-1, 1, N)
+    om = g.uniform(0.8, 1.6, 4)
+    ref = oracle.Problem(2, n, 9, d, sub)
+    h = nd.NDiag(2, n, 9, d, sub, "fp64")
+    xn = _t(np.zeros(N))
+    for mode in (nd.DECOMPOSED, nd.NATURAL):
+        for t in range(4):
+            h.sor_sweep(om, t, _t(b), _t(u), xn, mode=mode)
+            want = ref.sor_sweep(mode, t, om, b, u)
+            assert _rel(xn.cpu().numpy(), want) <= 1e-12, (mode, t)
+    h.close()
+
+
+@pytest.mark.parametrize("n,sub", CASES)
+def test_dilu_apply9_fp64(nd, n, sub):
+    d = _rand9(n, 93)
+    N = n[0] * n[1]
+    r = np.random.default_rng(94).uniform(-1, 1, N)
+    ref = oracle.Problem(2, n, 9, d, sub)
+    ref.ilu0_factor(oracle.DECOMPOSED)
+    h = nd.NDiag(2, n, 9, d, sub, "fp64")
+    h.ilu0_factor(nd.DECOMPOSED)
+    z = _t(np.zeros(N))
+    h.ilu0_apply(_t(r), z)
+    assert _rel(z.cpu().numpy(), ref.ilu0_apply(r)) <= 1e-12
+    h.close()
+
+
+def test_sweeps9_fp32(nd):
+    import torch
+    n, sub = (33, 25), (3, 2)
+    d = _rand9(n, 95)
+    N = n[0] * n[1]
+    g = np.random.default_rng(96)
+    b, u = g.uniform(-1, 1, N), g.uniform(-1, 1, N)
+    ref = oracle.Problem(2, n, 9, d, sub)
+    h = nd.NDiag(2, n, 9, d, sub, "fp32")
+    f32 = torch.float32
+    xn = _t(np.zeros(N), f32)
+    h.sor_sweep(1.1, 2, _t(b, f32), _t(u, f32), xn)
+    assert _rel(xn.cpu().numpy(), ref.sor_sweep(oracle.DECOMPOSED, 2, 1.1, b, u)) <= 2e-5
+    h.ilu0_factor(nd.DECOMPOSED)
+    ref.ilu0_factor(oracle.DECOMPOSED)
+    z = _t(np.zeros(N), f32)
+    h.ilu0_apply(_t(b, f32), z)
+    assert _rel(z.cpu().numpy(), ref.ilu0_apply(b)) <= 2e-5
+    h.close()
+
+
+def test_bicgstab_dilu9_convdiff_in_oracle_envelope(nd):
+    n, sub = 48, (3, 3)
+    d = W.convdiff9(n, 7.0, 0.6)
+    N = n * n
+    b = W.uniform_rhs(N, 1005)
+    ref = oracle.Problem(2, (n, n), 9, d, sub)
+    ref.ilu0_factor(oracle.DECOMPOSED)
+    counts = []
+    g = np.random.default_rng(12345)
+    for j in range(7):
+        bb = b if j == 0 else b * (1.0 + 1e-15 * g.standard_normal(N))
+        _, info = ref.solve(oracle.BICGSTAB, oracle.PREC_ILU0, oracle.DECOMPOSED, 1.0, 1e-8, 5000, bb)
+        counts.append(info["iters"])
+    h = nd.NDiag(2, (n, n), 9, d, sub, "fp64")
+    h.ilu0_factor(nd.DECOMPOSED)
+    x = _t(np.zeros(N))
+    info = h.solve(nd.BICGSTAB, nd.PREC_ILU0, _t(b), x, rtol=1e-8, maxit=5000)
+    assert info["relres"] <= 1e-8
+    assert min(counts) - 1 <= info["iters"] <= max(counts) + 1, (info, counts)
+    r = b - ref.matvec(x.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-8
+    h.close()
+
+
+def test_nine_point_ssor_and_natural_ilu_are_refused(nd):
+    n = (12, 10)
+    d = _rand9(n, 97)
+    h = nd.NDiag(2, n, 9, d, (2, 2), "fp64")
+    z = _t(np.zeros(120))
+    with pytest.raises(nd.NdiagError):
+        h.ssor_apply(1.0, _t(np.ones(120)), z)
+    with pytest.raises(nd.NdiagError):
+        h.ilu0_factor(nd.NATURAL)
+    h.close()
