@@ -259,6 +259,55 @@ int64_t ndiag_batch_cells(const ndiag_batch* b);
 int64_t ndiag_batch_launches(const ndiag_batch* b);
 void ndiag_batch_destroy(ndiag_batch* b);
 
+/*
+ * Solve server with continuous batching (no counterpart in the paper).
+ *   ndiag_server_create  slots = concurrent solves (worker threads, each with
+ *                        its own CUDA stream, 1..64); mem_budget = device
+ *                        bytes the running solves may hold (0: 80 % of the
+ *                        free memory now).
+ *   serve_submit         copies the request (HOST diags s x N and b) and
+ *                        queues it; *ticket identifies it. A queued request is
+ *                        admitted when a slot is free and its estimated memory
+ *                        fits the remaining budget (first fitting request in
+ *                        arrival order; one larger than the whole budget runs
+ *                        alone). Always decomposed ordering with sub[];
+ *                        ILU0 requests are factored first.
+ *   serve_poll           NDIAG_EBUSY while the request is queued or running;
+ *                        then fills *out, copies x (HOST, N doubles) if x is
+ *                        not NULL, and forgets the ticket.
+ *   ndiag_server_wait    blocks until the request is done or timeout_s passed
+ *                        (NDIAG_EBUSY).
+ *   ndiag_server_destroy finishes the queued requests, then stops.
+ */
+typedef struct ndiag_server ndiag_server;
+typedef struct {
+  int dim, stencil;
+  int64_t n[3];
+  int sub[3];
+  const double* diags; /* HOST, stencil x N, diagonal-major */
+  const double* b;     /* HOST, N */
+  int method, precond, precision;
+  double rtol;
+  int maxit;
+  double omega;        /* SSOR factor (<= 0: 1) */
+} ndiag_request;
+typedef struct {
+  int status;
+  ndiag_solve_info info;
+  double queue_s, run_s, latency_s; /* submit -> start, start -> end, submit -> end */
+  int64_t cells;
+} ndiag_result;
+typedef struct {
+  int queued, running, max_running;
+  int64_t solved, budget_bytes, in_use_bytes;
+} ndiag_server_stats_t;
+ndiag_status ndiag_server_create(ndiag_server** out, int slots, size_t mem_budget);
+ndiag_status serve_submit(ndiag_server* s, const ndiag_request* req, uint64_t* ticket);
+ndiag_status serve_poll(ndiag_server* s, uint64_t ticket, ndiag_result* out, double* x);
+ndiag_status ndiag_server_wait(ndiag_server* s, uint64_t ticket, double timeout_s);
+ndiag_status ndiag_server_stats(ndiag_server* s, ndiag_server_stats_t* out);
+void ndiag_server_destroy(ndiag_server* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,6 +15,9 @@ static ndiag_alloc_fn g_alloc = nullptr;
 static ndiag_free_fn g_free = nullptr;
 static void* g_alloc_ctx = nullptr;
 static std::mutex g_alloc_mu;
+static thread_local bool g_tls_plain_alloc = false;  // this thread ignores the allocator hooks
+
+void use_plain_allocator_on_this_thread(bool on) { g_tls_plain_alloc = on; }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -30,7 +33,7 @@ void* dev_alloc(size_t bytes, cudaStream_t s) {
   void* ctx;
   {
     std::lock_guard<std::mutex> lk(g_alloc_mu);
-    a = g_alloc;
+    a = g_tls_plain_alloc ? nullptr : g_alloc;
     ctx = g_alloc_ctx;
   }
   if (a) return a(bytes, (void*)s, ctx);
@@ -49,7 +52,7 @@ void dev_free(void* p, size_t bytes, cudaStream_t s) {
   void* ctx;
   {
     std::lock_guard<std::mutex> lk(g_alloc_mu);
-    f = g_free;
+    f = g_tls_plain_alloc ? nullptr : g_free;
     ctx = g_alloc_ctx;
   }
   if (f) {

@@ -29,6 +29,8 @@ ndiag_status cuda_status(cudaError_t e, const char* what);
   } while (0)
 
 void* dev_alloc(size_t bytes, cudaStream_t s);
+// Threads of the server allocate with cudaMallocAsync even when hooks are set.
+void use_plain_allocator_on_this_thread(bool on);
 void dev_free(void* p, size_t bytes, cudaStream_t s);
 
 // Stencil entries (diagonal-major storage order of the C ABI).

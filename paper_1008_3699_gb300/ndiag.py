@@ -29,7 +29,9 @@ EXPORTED = ["ndiag_set_allocator", "ndiag_last_error", "ndiag_create", "ndiag_de
             "ndiag_precision", "sor_sweep", "ssor_apply", "ilu0_factor", "ilu0_apply", "ndiag_residual",
             "krylov_solve", "ndiag_profile", "ndiag_read_counters", "ilu0_apply_noalloc",
             "ndiag_batch_create", "ndiag_batch_autotune", "ndiag_batch_tiles", "ndiag_batch_solve",
-            "ndiag_batch_cells", "ndiag_batch_launches", "ndiag_batch_destroy"]
+            "ndiag_batch_cells", "ndiag_batch_launches", "ndiag_batch_destroy",
+            "ndiag_server_create", "serve_submit", "serve_poll", "ndiag_server_wait", "ndiag_server_stats",
+            "ndiag_server_destroy"]
 NOALLOC_MAX_CELLS = 1 << 20
 
 
@@ -43,6 +45,23 @@ class NdiagError(RuntimeError):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer", ctypes.c_int), ("relres", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("stencil", ctypes.c_int), ("n", ctypes.c_int64 * 3),
+                ("sub", ctypes.c_int * 3), ("diags", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("method", ctypes.c_int), ("precond", ctypes.c_int), ("precision", ctypes.c_int),
+                ("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("omega", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("info", SolveInfo), ("queue_s", ctypes.c_double),
+                ("run_s", ctypes.c_double), ("latency_s", ctypes.c_double), ("cells", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int), ("running", ctypes.c_int), ("max_running", ctypes.c_int),
+                ("solved", ctypes.c_int64), ("budget_bytes", ctypes.c_int64), ("in_use_bytes", ctypes.c_int64)]
 
 
 class Counters(ctypes.Structure):
@@ -93,6 +112,13 @@ def load(path: str = LIB_PATH):
     L.ndiag_batch_launches.restype = L64
     L.ndiag_batch_destroy.argtypes = [P]
     L.ndiag_batch_destroy.restype = None
+    L.ndiag_server_create.argtypes = [ctypes.POINTER(P), I, ctypes.c_size_t]
+    L.serve_submit.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    L.serve_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(Result), P]
+    L.ndiag_server_wait.argtypes = [P, ctypes.c_uint64, D]
+    L.ndiag_server_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+    L.ndiag_server_destroy.argtypes = [P]
+    L.ndiag_server_destroy.restype = None
     if path == LIB_PATH:
         _lib = L
     return L
@@ -272,6 +298,73 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             self.L.ndiag_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_d16": 2}
+
+
+class Server:
+    """Continuous-batching solve server: submit() queues a request, poll() /
+    wait() collect the result. Requests run concurrently in `slots` workers,
+    admitted when a slot is free and their memory fits the budget."""
+
+    def __init__(self, slots=4, mem_budget=0):
+        self.L = load()
+        h = ctypes.c_void_p()
+        _check(self.L, self.L.ndiag_server_create(ctypes.byref(h), int(slots), int(mem_budget)))
+        self.h = h
+        self._sizes = {}
+
+    def submit(self, problem, method=PCG, precond=PREC_SSOR, precision="fp64", rtol=1e-8, maxit=20000,
+               omega=1.0):
+        dim = int(problem["dim"])
+        n = list(problem["n"]) + [1, 1, 1]
+        sub = list(problem.get("sub", (1, 1, 1))) + [1, 1, 1]
+        diags = np.ascontiguousarray(problem["diags"], dtype=np.float64)
+        b = np.ascontiguousarray(problem["b"], dtype=np.float64)
+        r = Request(dim, int(problem["stencil"]), (ctypes.c_int64 * 3)(*n[:3]), (ctypes.c_int * 3)(*sub[:3]),
+                    diags.ctypes.data, b.ctypes.data, int(method), int(precond), PRECISIONS[precision],
+                    float(rtol), int(maxit), float(omega))
+        t = ctypes.c_uint64()
+        _check(self.L, self.L.serve_submit(self.h, ctypes.byref(r), ctypes.byref(t)))
+        self._sizes[t.value] = b.size
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else (result dict, x as numpy)."""
+        res = Result()
+        x = np.empty(self._sizes[ticket])
+        st = self.L.serve_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(res), x.ctypes.data_as(ctypes.c_void_p))
+        if st == EBUSY:
+            return None
+        _check(self.L, st)
+        del self._sizes[ticket]
+        i = res.info
+        return (dict(status=STATUS_NAMES[res.status], iters=i.iterations, outer=i.outer, relres=i.relres,
+                     queue_s=res.queue_s, run_s=res.run_s, latency_s=res.latency_s, cells=res.cells), x)
+
+    def wait(self, ticket, timeout=600.0):
+        st = self.L.ndiag_server_wait(self.h, ctypes.c_uint64(ticket), float(timeout))
+        if st not in (OK, EBUSY):
+            _check(self.L, st)
+        return self.poll(ticket) if st == OK else None
+
+    def stats(self):
+        s = ServerStats()
+        _check(self.L, self.L.ndiag_server_stats(self.h, ctypes.byref(s)))
+        return dict(queued=s.queued, running=s.running, max_running=s.max_running, solved=s.solved,
+                    budget_bytes=s.budget_bytes, in_use_bytes=s.in_use_bytes)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ndiag_server_destroy(self.h)
             self.h = None
 
     def __del__(self):
