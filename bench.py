@@ -35,8 +35,8 @@ sys.path.insert(0, ROOT)
 N_SIDE, SUB = 2048, 16
 WORKLOAD = "varcoef2d-2048x2048-5pt-fp64-ilu0-bicgstab-16x16"
 METRIC = "Gcell-updates/s per sweep (% HBM peak); solves/s and p99 latency at rel-res 1e-8"
-SWEEP_SRC = os.path.join(ROOT, "paper_1008_3699_gb300", "csrc", "sweep2d.cu")
-PROFILE = os.path.join(ROOT, "profiles", "sweep2d_ilu0_varcoef2048.md")
+SWEEP_SRC = os.path.join(ROOT, "paper_1008_3699_gb300", "csrc", "sweep2d_staged.cu")
+PROFILE = os.path.join(ROOT, "profiles", "sweep2d_staged_ilu0_varcoef2048.md")
 
 
 def measured_peaks():
@@ -129,6 +129,18 @@ def cpu_baseline(problem, iters=6):
                       f"({sweeps} sweeps, {dt:.1f} s, 1 thread)"}
 
 
+def over_ranks(ms, updates, dist, device):
+    """Whole-job timing of replicas: the slowest rank's time and the cell
+    updates of all ranks (dist = torch.distributed or None)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([updates], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -165,9 +177,15 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--kernel-only", type=int, default=0, metavar="K",
                     help="only factor and run K ILU(0) applies of the workload (for kernel profiling)")
+    ap.add_argument("--workload", default="varcoef2048",
+                    choices=["varcoef2048", "poisson64", "poisson3d256", "batch512", "serving"],
+                    help="varcoef2048 is the benchmark; the others print one measurement line each")
+    ap.add_argument("--serving-requests", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "varcoef2048":
+        return EXTRA[args.workload](args)
 
     import numpy as np
     import torch
@@ -240,14 +258,9 @@ def main():
         clk = clocks.stop()
         cnt = h.counters()
         lat = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-        total_ms = ev[0].elapsed_time(ev[-1])
-        tmax = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        updates = torch.tensor([float(N) * cnt["sweep_launches"]], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-            dist.all_reduce(updates, op=dist.ReduceOp.SUM)
-        total_ms = float(tmax.item())
-        value = float(updates.item()) / (total_ms / 1e3) / 1e9
+        total_ms, all_updates = over_ranks(ev[0].elapsed_time(ev[-1]), float(N) * cnt["sweep_launches"], dist,
+                                           "cuda")
+        value = all_updates / (total_ms / 1e3) / 1e9
 
         # end to end through the C ABI with pinned host buffers
         hb = torch.empty(N, dtype=torch.float64, pin_memory=True)
@@ -316,7 +329,7 @@ def main():
         "relres": max(i["relres"] for i in infos),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": kernel_traffic(),
-                     "kernel": "sweep2d_kernel (ILU(0) apply and factor sweeps)",
+                     "kernel": "sweep2d_staged_kernel (ILU(0) apply sweeps; factor sweep in sweep2d_kernel)",
                      "peak_kind": peak_kind, "sweep_launches": cnt["sweep_launches"],
                      "sweep_ms": cnt["sweep_ms"], "sweep_bytes": cnt["sweep_bytes"]},
         "sweep_share_of_step": cnt["sweep_ms"] / total_ms if total_ms else None,
@@ -329,6 +342,158 @@ def main():
         "natural_ilu0": natural,
     }
     print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# The other workloads: one JSON measurement line each (not the benchmark line).
+# ---------------------------------------------------------------------------
+
+def _setup():
+    import torch
+    from paper_1008_3699_gb300 import build as nd_build
+    from paper_1008_3699_gb300 import ndiag as nd
+    from paper_1008_3699_gb300 import workloads as W
+    nd_build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    return torch, nd, W
+
+
+def _timed_solve(torch, h, *a, **kw):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = h.solve(*a, **kw)
+    torch.cuda.synchronize()
+    info["wall_s"] = time.perf_counter() - t0
+    return info
+
+
+def workload_poisson64(args):
+    """64 x 64 Poisson, 2 x 2 subdomains: decomposed and natural-order SOR as
+    stationary solvers to rel-res 1e-8 with omega = 2/(1+sin(pi/65))."""
+    torch, nd, W = _setup()
+    p = W.poisson64_problem()
+    out = {}
+    for name, mode, sub in (("decomposed", nd.DECOMPOSED, p["sub"]), ("natural", nd.NATURAL, (1, 1, 1))):
+        h = nd.NDiag(2, p["n"], 5, p["diags"], sub, "fp64")
+        b = torch.tensor(p["b"], device="cuda")
+        for k in range(args.warmup + 1):
+            x = torch.zeros_like(b)
+            info = _timed_solve(torch, h, nd.STATIONARY, nd.PREC_NONE, b, x, rtol=1e-8, maxit=20000,
+                                omega=p["omega"], mode=mode)
+        out[name] = {k: info[k] for k in ("iters", "relres", "wall_s")}
+        h.close()
+    print(json.dumps({"workload": "poisson2d-64x64-5pt-fp64-sor-2x2", "metric": "SOR sweeps to rel-res 1e-8",
+                      "omega": p["omega"], **out}))
+
+
+def workload_poisson3d256(args):
+    """256^3 Poisson, 8 x 8 x 8 subdomains: SSOR-PCG with fp32 sweeps and fp64
+    refinement, and the same in fp64, to rel-res 1e-8; SSOR apply time."""
+    torch, nd, W = _setup()
+    p = W.poisson3d_problem(256, 8)
+    N = 256 ** 3
+    out = {}
+    for prec in ("fp32", "fp64"):
+        h = nd.NDiag(3, p["n"], 7, p["diags"], p["sub"], prec)
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        r = torch.tensor(p["b"], device="cuda", dtype=dt)
+        z = torch.empty_like(r)
+        for _ in range(max(2, args.warmup)):
+            h.ssor_apply(1.0, r, z)
+        h.profile(True)
+        for _ in range(5):
+            h.ssor_apply(1.0, r, z)
+        c = h.counters()
+        b = torch.tensor(p["b"], device="cuda")
+        x = torch.zeros_like(b)
+        info = _timed_solve(torch, h, nd.PCG, nd.PREC_SSOR, b, x, rtol=1e-8, maxit=5000)
+        out[prec] = {"ssor_apply_ms": c["sweep_ms"] / 5, "sweep_gcell_per_s": 2 * N * 5 / c["sweep_ms"] / 1e6,
+                     **{k: info[k] for k in ("iters", "outer", "relres", "wall_s")}}
+        h.close()
+    print(json.dumps({"workload": "poisson3d-256^3-7pt-ssor-pcg-8x8x8", "metric": "solve seconds to rel-res 1e-8",
+                      **out}))
+
+
+def workload_batch512(args):
+    """512 variable-coefficient 5-point problems (sides U[32,512]): the batched
+    fp32 + fp64-refinement SSOR-PCG (autotuned tile, graph-captured chunks)
+    against plain fp64 solves of one problem per handle."""
+    torch, nd, W = _setup()
+    import numpy as np
+    probs = W.batched_problems(512, 32, 512, 1004)
+    b = torch.tensor(np.concatenate([q["b"] for q in probs]), device="cuda")
+    B = nd.Batch(probs, tile=64)
+    B.autotune(b)
+    for k in range(2):
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = B.solve(b, x, rtol=1e-8)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    line = {"workload": "batch-512x2d-5pt-U[32,512]-fp32+fp64ref-ssor-pcg", "metric": "solves/s at rel-res 1e-8",
+            "batched": {"solves_per_s": len(probs) / dt, "seconds": dt, "tile": int(B.tiles()[0]),
+                        "relres_max": max(i["relres"] for i in infos),
+                        "iters_mean": float(np.mean([i["iters"] for i in infos])), "launches": B.launches()}}
+    B.close()
+    tot, its = 0.0, []
+    for q in probs:
+        sub = (max(1, -(-q["n"][0] // 64)), max(1, -(-q["n"][1] // 64)))
+        h = nd.NDiag(2, q["n"], 5, q["diags"], sub, "fp64")
+        bk = torch.tensor(q["b"], device="cuda")
+        info = _timed_solve(torch, h, nd.PCG, nd.PREC_SSOR, bk, torch.zeros_like(bk), rtol=1e-8, maxit=20000)
+        tot += info["wall_s"]
+        its.append(info["iters"])
+        h.close()
+    line["fp64_one_per_handle"] = {"solves_per_s": len(probs) / tot, "seconds": tot,
+                                   "iters_mean": float(np.mean(its))}
+    print(json.dumps(line))
+
+
+def workload_serving(args):
+    """Poisson arrivals (2000 req/s) of 9-point convection-diffusion (ILU(0)-
+    BiCGSTAB, fp64) and 3D Poisson (SSOR-PCG, fp32 + refinement) requests
+    through the solve server; solves/s and p50/p99 latency."""
+    torch, nd, W = _setup()
+    import numpy as np
+    count = args.serving_requests
+    t_arr, specs = W.serving_trace(count, 2000.0, 1005)
+    reqs = []
+    for sp in specs:
+        r = W.build_request(sp)
+        n = r["n"][0]
+        if r["stencil"] == 9:
+            k = max(1, -(-n // 128))
+            r["sub"] = (k, k, 1)
+            kw = dict(method=nd.BICGSTAB, precond=nd.PREC_ILU0, precision="fp64")
+        else:
+            k = max(1, -(-n // 32))
+            r["sub"] = (k, k, k)
+            kw = dict(method=nd.PCG, precond=nd.PREC_SSOR, precision="fp32")
+        reqs.append((r, kw))
+    S = nd.Server(slots=8)
+    t0 = time.perf_counter()
+    tickets = []
+    for k in range(count):
+        d = t0 + t_arr[k] - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        tickets.append(S.submit(reqs[k][0], **reqs[k][1]))
+    res = [S.wait(t, timeout=1800) for t in tickets]
+    span = time.perf_counter() - t0
+    st = S.stats()
+    S.close()
+    lat = np.array([r["latency_s"] for r, _ in res])
+    print(json.dumps({"workload": f"serving-{count}-requests-poisson-arrivals-2000/s",
+                      "metric": "solves/s; p50/p99 latency at rel-res 1e-8",
+                      "solves_per_s": count / span, "p50_latency_s": float(np.percentile(lat, 50)),
+                      "p99_latency_s": float(np.percentile(lat, 99)),
+                      "ok": sum(r["status"] == "OK" for r, _ in res),
+                      "relres_max": max(r["relres"] for r, _ in res), "max_running": st["max_running"]}))
+
+
+EXTRA = {"poisson64": workload_poisson64, "poisson3d256": workload_poisson3d256,
+         "batch512": workload_batch512, "serving": workload_serving}
 
 
 if __name__ == "__main__":

@@ -8,6 +8,16 @@ namespace nd {
 
 namespace {
 constexpr int BT = 256;  // threads per block
+constexpr int BPS = 4;   // resident blocks per SM the kernels are bounded for (64 registers)
+// Elements per thread per loop trip. Each trip issues all its loads before any
+// arithmetic or store, so a thread keeps U loads per stream in flight; with
+// BPS x BT threads per SM that is enough to cover HBM latency on GB300.
+constexpr int U = 4;
+constexpr int BPS_STENCIL = 3;  // the stencil kernels hold ten loads per cell, two cells per thread
+
+#define ND_STREAM_LOOP(N)                                                              \
+  for (int64_t base = (int64_t)blockIdx.x * (BT * U) + threadIdx.x; base < (N);        \
+       base += (int64_t)gridDim.x * (BT * U))
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -52,13 +62,17 @@ struct Geo {
 };
 
 // (A x)_i for a structured stencil; the matrix A is diagonal-major (s, N).
-template <class T, class TA>
+// IDX is the index type of the cell coordinates: 32-bit division whenever the
+// grid has fewer than 2^31 cells.
+template <class T, class TA, class IDX>
 __device__ __forceinline__ T stencil_apply(const Geo& g, const TA* __restrict__ A, const T* __restrict__ x,
                                            int64_t i) {
-  const int cx = (int)(i % g.nx);
-  const int64_t rest = i / g.nx;
-  const int cy = (int)(rest % g.ny);
-  const int cz = (int)(rest / g.ny);
+  const IDX ii = (IDX)i, nx = (IDX)g.nx, ny = (IDX)g.ny;
+  const IDX rest = ii / nx;
+  const int cx = (int)(ii - rest * nx);
+  const IDX rz = rest / ny;
+  const int cy = (int)(rest - rz * ny);
+  const int cz = (int)rz;
   const int64_t N = g.N;
   T acc = (T)A[i] * x[i];
   if (cx > 0) acc = fma((T)A[N + i], x[i - 1], acc);
@@ -78,16 +92,33 @@ __device__ __forceinline__ T stencil_apply(const Geo& g, const TA* __restrict__ 
   return acc;
 }
 
-// y = A x ; ND = 1: partial (w, y); ND = 2: also (y, y)
-template <class T, class TA, int ND>
-__global__ void __launch_bounds__(BT) spmv_kernel(Geo g, const TA* __restrict__ A, const T* __restrict__ x,
-                                                  T* __restrict__ y, const T* __restrict__ w, Reduce R) {
+// y = A x ; ND = 1: partial (w, y); ND = 2: also (y, y). Two cells per thread
+// per trip (the stencil reads ten values per cell).
+template <class T, class TA, int ND, class IDX>
+__global__ void __launch_bounds__(BT, BPS_STENCIL) spmv_kernel(Geo g, const TA* __restrict__ A, const T* __restrict__ x,
+                                                       T* __restrict__ y, const T* __restrict__ w, Reduce R) {
+  constexpr int V = 2;
   double d0 = 0.0, d1 = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < g.N; i += (int64_t)gridDim.x * BT) {
-    const T v = stencil_apply<T, TA>(g, A, x, i);
-    y[i] = v;
-    if (ND >= 1) d0 += (double)w[i] * (double)v;
-    if (ND >= 2) d1 += (double)v * (double)v;
+  for (int64_t base = (int64_t)blockIdx.x * (BT * V) + threadIdx.x; base < g.N;
+       base += (int64_t)gridDim.x * (BT * V)) {
+    T v[V], wv[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < g.N) {
+        v[u] = stencil_apply<T, TA, IDX>(g, A, x, i);
+        if (ND >= 1) wv[u] = w[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < g.N) {
+        y[i] = v[u];
+        if (ND >= 1) d0 += (double)wv[u] * (double)v[u];
+        if (ND >= 2) d1 += (double)v[u] * (double)v[u];
+      }
+    }
   }
   if (ND == 1) {
     double vv[1] = {d0};
@@ -99,15 +130,29 @@ __global__ void __launch_bounds__(BT) spmv_kernel(Geo g, const TA* __restrict__ 
 }
 
 // r = b - A x (fp64), ||r||^2
-template <class TB>
-__global__ void __launch_bounds__(BT) residual_kernel(Geo g, const double* __restrict__ A,
-                                                      const double* __restrict__ b, const double* __restrict__ x,
-                                                      TB* __restrict__ r, Reduce R) {
+template <class TB, class IDX>
+__global__ void __launch_bounds__(BT, BPS_STENCIL) residual_kernel(Geo g, const double* __restrict__ A,
+                                                           const double* __restrict__ b,
+                                                           const double* __restrict__ x, TB* __restrict__ r,
+                                                           Reduce R) {
+  constexpr int V = 2;
   double d = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < g.N; i += (int64_t)gridDim.x * BT) {
-    const double v = b[i] - stencil_apply<double, double>(g, A, x, i);
-    r[i] = (TB)v;
-    d += v * v;
+  for (int64_t base = (int64_t)blockIdx.x * (BT * V) + threadIdx.x; base < g.N;
+       base += (int64_t)gridDim.x * (BT * V)) {
+    double v[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < g.N) v[u] = b[i] - stencil_apply<double, double, IDX>(g, A, x, i);
+    }
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < g.N) {
+        r[i] = (TB)v[u];
+        d += v[u] * v[u];
+      }
+    }
   }
   double vv[1] = {d};
   finish_reduce<1>(vv, R);
@@ -115,14 +160,28 @@ __global__ void __launch_bounds__(BT) residual_kernel(Geo g, const double* __res
 
 // generic fused dots: up to 3 inner products (a_k, b_k)
 template <class T, int NV>
-__global__ void __launch_bounds__(BT) dots_kernel(int64_t N, const T* a0, const T* b0, const T* a1, const T* b1,
-                                                  const T* a2, const T* b2, Reduce R) {
+__global__ void __launch_bounds__(BT, BPS) dots_kernel(int64_t N, const T* __restrict__ a0,
+                                                       const T* __restrict__ b0, const T* __restrict__ a1,
+                                                       const T* __restrict__ b1, const T* __restrict__ a2,
+                                                       const T* __restrict__ b2, Reduce R) {
   double d[NV];
   for (int k = 0; k < NV; ++k) d[k] = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT) {
-    d[0] += (double)a0[i] * (double)b0[i];
-    if (NV > 1) d[1] += (double)a1[i] * (double)b1[i];
-    if (NV > 2) d[2] += (double)a2[i] * (double)b2[i];
+  constexpr int U = NV > 2 ? 2 : 4;
+  ND_STREAM_LOOP(N) {
+    T va[NV][U], vb[NV][U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < N) {
+        va[0][u] = a0[i], vb[0][u] = b0[i];
+        if (NV > 1) va[1 % NV][u] = a1[i], vb[1 % NV][u] = b1[i];
+        if (NV > 2) va[2 % NV][u] = a2[i], vb[2 % NV][u] = b2[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (base + u * BT < N)
+        for (int k = 0; k < NV; ++k) d[k] += (double)va[k][u] * (double)vb[k][u];
   }
   finish_reduce<NV>(d, R);
 }
@@ -130,96 +189,218 @@ __global__ void __launch_bounds__(BT) dots_kernel(int64_t N, const T* a0, const 
 // ---- BiCGSTAB steps (scalars live in device memory) ----
 // p = r + beta (p - om v),  beta = (rho/rho_old)(alpha/om)
 template <class T>
-__global__ void __launch_bounds__(BT) bicg_p_kernel(int64_t N, const T* r, T* p, const T* v, const double* sc,
-                                                    int first) {
+__global__ void __launch_bounds__(BT, BPS) bicg_p_kernel(int64_t N, const T* __restrict__ r, T* __restrict__ p,
+                                                         const T* __restrict__ v, const double* sc, int first) {
   const double rho = sc[SC_RHO], rho_old = sc[SC_RHO_OLD], alpha = sc[SC_ALPHA], om = sc[SC_OM];
   const double beta = first ? 0.0 : (rho / rho_old) * (alpha / om);
-  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT) {
-    p[i] = first ? r[i] : (T)((double)r[i] + beta * ((double)p[i] - om * (double)v[i]));
+  ND_STREAM_LOOP(N) {
+    T vr[U], vp[U], vv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < N) {
+        vr[u] = r[i];
+        if (!first) vp[u] = p[i], vv[u] = v[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < N) p[i] = first ? vr[u] : (T)((double)vr[u] + beta * ((double)vp[u] - om * (double)vv[u]));
+    }
   }
 }
 // s = r - alpha v, alpha = rho / (rh, v); ||s||^2
 template <class T>
-__global__ void __launch_bounds__(BT) bicg_s_kernel(int64_t N, const T* r, const T* v, T* s, const double* sc,
-                                                    Reduce R) {
+__global__ void __launch_bounds__(BT, BPS) bicg_s_kernel(int64_t N, const T* __restrict__ r,
+                                                         const T* __restrict__ v, T* __restrict__ s,
+                                                         const double* sc, Reduce R) {
   const double alpha = sc[SC_RHO] / sc[SC_RV];
   double d = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT) {
-    const T sv = (T)((double)r[i] - alpha * (double)v[i]);
-    s[i] = sv;
-    d += (double)sv * (double)sv;
+  ND_STREAM_LOOP(N) {
+    T vr[U], vv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < N) vr[u] = r[i], vv[u] = v[i];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < N) {
+        const T sv = (T)((double)vr[u] - alpha * (double)vv[u]);
+        s[i] = sv;
+        d += (double)sv * (double)sv;
+      }
+    }
   }
   double vv[1] = {d};
   finish_reduce<1>(vv, R);
 }
 // x += alpha ph + om sh ; r = s - om t ; ||r||^2, (rh, r)
 template <class T>
-__global__ void __launch_bounds__(BT) bicg_xr_kernel(int64_t N, T* x, const T* ph, const T* sh, T* r, const T* s,
-                                                     const T* t, const T* rh, const double* sc, Reduce R) {
-  const double alpha = sc[SC_RHO] / sc[SC_RV];
+__global__ void __launch_bounds__(BT, BPS) bicg_xr_kernel(int64_t N, T* __restrict__ x, const T* __restrict__ ph,
+                                                          const T* __restrict__ sh, T* __restrict__ r,
+                                                          const T* __restrict__ s, const T* __restrict__ t,
+                                                          const T* __restrict__ rh, const double* sc, Reduce R) {
+  // Breakdown of the first half step (rho = 0, (rh, v) = 0 or a non-finite s)
+  // leaves x and r as they are; the host reports it. A first half step that
+  // already meets the tolerance (||s||^2 <= tol^2) takes om = 0: x += alpha ph
+  // and r = s, the solution of the half step.
+  const double rho = sc[SC_RHO], rv = sc[SC_RV], ss = sc[SC_SS];
+  if (rho == 0.0 || rv == 0.0 || !isfinite(ss)) return;
+  const double alpha = rho / rv;
   const double tt = sc[SC_TT];
-  const double om = tt == 0.0 ? 0.0 : sc[SC_TS] / tt;
+  const double om = (ss <= sc[SC_TOL2] || tt == 0.0) ? 0.0 : sc[SC_TS] / tt;
   double d0 = 0.0, d1 = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT) {
-    x[i] = (T)((double)x[i] + alpha * (double)ph[i] + om * (double)sh[i]);
-    const T rv = (T)((double)s[i] - om * (double)t[i]);
-    r[i] = rv;
-    d0 += (double)rv * (double)rv;
-    d1 += (double)rh[i] * (double)rv;
+  constexpr int U = 2;  // six streams
+  ND_STREAM_LOOP(N) {
+    T vx[U], vph[U], vsh[U], vs[U], vt[U], vrh[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < N) vx[u] = x[i], vph[u] = ph[i], vsh[u] = sh[i], vs[u] = s[i], vt[u] = t[i], vrh[u] = rh[i];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < N) {
+        x[i] = (T)((double)vx[u] + alpha * (double)vph[u] + om * (double)vsh[u]);
+        const T rv = (T)((double)vs[u] - om * (double)vt[u]);
+        r[i] = rv;
+        d0 += (double)rv * (double)rv;
+        d1 += (double)vrh[u] * (double)rv;
+      }
+    }
   }
   double vv[2] = {d0, d1};
   finish_reduce<2>(vv, R);
 }
 // x += alpha ph  (exit at the half step)
 template <class T>
-__global__ void __launch_bounds__(BT) axpy_alpha_kernel(int64_t N, T* x, const T* ph, const double* sc) {
+__global__ void __launch_bounds__(BT, BPS) axpy_alpha_kernel(int64_t N, T* __restrict__ x,
+                                                             const T* __restrict__ ph, const double* sc) {
   const double alpha = sc[SC_RHO] / sc[SC_RV];
-  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT)
-    x[i] = (T)((double)x[i] + alpha * (double)ph[i]);
+  ND_STREAM_LOOP(N) {
+    T vx[U], vp[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < N) vx[u] = x[i], vp[u] = ph[i];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < N) x[i] = (T)((double)vx[u] + alpha * (double)vp[u]);
+    }
+  }
 }
 
 // ---- PCG steps ----
 // x += alpha p ; r -= alpha q ; ||r||^2 ; alpha = rz / (p, q)
 template <class T>
-__global__ void __launch_bounds__(BT) cg_xr_kernel(int64_t N, T* x, const T* p, T* r, const T* q, const double* sc,
-                                                   Reduce R) {
+__global__ void __launch_bounds__(BT, BPS) cg_xr_kernel(int64_t N, T* __restrict__ x, const T* __restrict__ p,
+                                                        T* __restrict__ r, const T* __restrict__ q,
+                                                        const double* sc, Reduce R) {
   const double alpha = sc[SC_RZ] / sc[SC_PQ];
   double d = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT) {
-    x[i] = (T)((double)x[i] + alpha * (double)p[i]);
-    const T rv = (T)((double)r[i] - alpha * (double)q[i]);
-    r[i] = rv;
-    d += (double)rv * (double)rv;
+  constexpr int U = 3;  // four streams
+  ND_STREAM_LOOP(N) {
+    T vx[U], vp[U], vr[U], vq[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < N) vx[u] = x[i], vp[u] = p[i], vr[u] = r[i], vq[u] = q[i];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < N) {
+        x[i] = (T)((double)vx[u] + alpha * (double)vp[u]);
+        const T rv = (T)((double)vr[u] - alpha * (double)vq[u]);
+        r[i] = rv;
+        d += (double)rv * (double)rv;
+      }
+    }
   }
   double vv[1] = {d};
   finish_reduce<1>(vv, R);
 }
 // p = z + beta p, beta = rz_new / rz ; first: p = z
 template <class T>
-__global__ void __launch_bounds__(BT) cg_p_kernel(int64_t N, const T* z, T* p, const double* sc, int first) {
+__global__ void __launch_bounds__(BT, BPS) cg_p_kernel(int64_t N, const T* __restrict__ z, T* __restrict__ p,
+                                                       const double* sc, int first) {
   const double beta = first ? 0.0 : sc[SC_RZ_NEW] / sc[SC_RZ];
-  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT)
-    p[i] = first ? z[i] : (T)((double)z[i] + beta * (double)p[i]);
+  ND_STREAM_LOOP(N) {
+    T vz[U], vp[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < N) {
+        vz[u] = z[i];
+        if (!first) vp[u] = p[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * BT;
+      if (i < N) p[i] = first ? vz[u] : (T)((double)vz[u] + beta * (double)vp[u]);
+    }
+  }
 }
 
 __global__ void copy_scalar_kernel(double* sc, int dst, int src) { sc[dst] = sc[src]; }
 
 template <class TD, class TS>
-__global__ void __launch_bounds__(BT) convert_kernel(int64_t N, const TS* s, TD* d) {
-  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT) d[i] = (TD)s[i];
+__global__ void __launch_bounds__(BT, BPS) convert_kernel(int64_t N, const TS* __restrict__ s, TD* __restrict__ d) {
+  ND_STREAM_LOOP(N) {
+    TS v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (base + u * BT < N) v[u] = s[base + u * BT];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (base + u * BT < N) d[base + u * BT] = (TD)v[u];
+  }
 }
-__global__ void __launch_bounds__(BT) add_to_kernel(int64_t N, double* x, const float* e) {
-  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT) x[i] += (double)e[i];
+__global__ void __launch_bounds__(BT, BPS) add_to_kernel(int64_t N, double* __restrict__ x,
+                                                         const float* __restrict__ e) {
+  ND_STREAM_LOOP(N) {
+    double vx[U];
+    float ve[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (base + u * BT < N) vx[u] = x[base + u * BT], ve[u] = e[base + u * BT];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (base + u * BT < N) x[base + u * BT] = vx[u] + (double)ve[u];
+  }
 }
 template <class T>
-__global__ void __launch_bounds__(BT) scale_kernel(int64_t N, T* x, double f) {
-  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT)
-    x[i] = (T)((double)x[i] * f);
+__global__ void __launch_bounds__(BT, BPS) scale_kernel(int64_t N, T* __restrict__ x, double f) {
+  ND_STREAM_LOOP(N) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (base + u * BT < N) v[u] = x[base + u * BT];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (base + u * BT < N) x[base + u * BT] = (T)((double)v[u] * f);
+  }
 }
 template <class T>
-__global__ void __launch_bounds__(BT) mul_kernel(int64_t N, const double* A0, const T* x, T* y) {
-  for (int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x; i < N; i += (int64_t)gridDim.x * BT)
-    y[i] = (T)(A0[i] * (double)x[i]);
+__global__ void __launch_bounds__(BT, BPS) mul_kernel(int64_t N, const double* __restrict__ A0,
+                                                      const T* __restrict__ x, T* __restrict__ y) {
+  ND_STREAM_LOOP(N) {
+    double va[U];
+    T vx[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (base + u * BT < N) va[u] = A0[base + u * BT], vx[u] = x[base + u * BT];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (base + u * BT < N) y[base + u * BT] = (T)(va[u] * (double)vx[u]);
+  }
 }
 
 Geo geo(const Handle* h) {
@@ -227,9 +408,12 @@ Geo geo(const Handle* h) {
 }
 }  // namespace
 
+// One grid size for every vector kernel of a handle (a fixed function of N and
+// the SM count, so the reductions sum in a fixed order): BPS resident blocks
+// per SM, fewer when the vector is short.
 int grid_blocks(const Handle* h) {
-  const int64_t need = (h->N + BT - 1) / BT;
-  const int64_t cap = (int64_t)h->sm_count * 8;
+  const int64_t need = (h->N + BT * 2 - 1) / (BT * 2);
+  const int64_t cap = (int64_t)h->sm_count * BPS;
   return (int)(need < cap ? (need < 1 ? 1 : need) : cap);
 }
 
@@ -246,16 +430,33 @@ size_t reduce_bytes(const Handle* h) {
   return sizeof(double) * (RED_RES + (size_t)RED_SLOTS * 4 * grid_blocks(h));
 }
 
-#define LAUNCH(kern, ...) \
-  do {                                                          \
-    ++h->launches;                                              \
-    kern<<<grid_blocks(h), BT, 0, h->stream>>>(__VA_ARGS__);    \
-    ND_CUDA(cudaGetLastError());                                \
+#define LAUNCH_G(grid, kern, ...)                       \
+  do {                                                  \
+    ++h->launches;                                      \
+    kern<<<(grid), BT, 0, h->stream>>>(__VA_ARGS__);    \
+    ND_CUDA(cudaGetLastError());                        \
+  } while (0)
+#define LAUNCH(kern, ...) LAUNCH_G(grid_blocks(h), kern, __VA_ARGS__)
+
+// cell coordinates in 32-bit arithmetic when the grid allows it
+bool small_index(const Handle* h) { return h->N < ((int64_t)1 << 31); }
+
+#define ND_UNPAREN(...) __VA_ARGS__
+// the stencil kernels: at most BPS_STENCIL blocks per SM (a subset of the
+// partial slots of grid_blocks)
+int stencil_blocks(const Handle* h) {
+  const int g = grid_blocks(h), cap = h->sm_count * BPS_STENCIL;
+  return g < cap ? g : cap;
+}
+#define LAUNCH_IDX(kern, targs, ...)                                                                      \
+  do {                                                                                                    \
+    if (small_index(h)) LAUNCH_G(stencil_blocks(h), (kern<ND_UNPAREN targs, uint32_t>), __VA_ARGS__);     \
+    else LAUNCH_G(stencil_blocks(h), (kern<ND_UNPAREN targs, uint64_t>), __VA_ARGS__);                    \
   } while (0)
 
 ndiag_status spmv64(Handle* h, const double* x, double* y) {
   Reduce R{};
-  LAUNCH((spmv_kernel<double, double, 0>), geo(h), h->A64, x, y, (const double*)nullptr, R);
+  LAUNCH_IDX(spmv_kernel, (double, double, 0), geo(h), h->A64, x, y, (const double*)nullptr, R);
   return NDIAG_OK;
 }
 
@@ -264,11 +465,11 @@ ndiag_status spmv_dot(Handle* h, const T* x, T* y, const T* w, double* res, int 
   Reduce R = reduce_slot(h, slot);
   R.res = res;
   if (sizeof(T) == 8) {
-    if (two) LAUNCH((spmv_kernel<T, double, 2>), geo(h), h->A64, x, y, w, R);
-    else LAUNCH((spmv_kernel<T, double, 1>), geo(h), h->A64, x, y, w, R);
+    if (two) LAUNCH_IDX(spmv_kernel, (T, double, 2), geo(h), h->A64, x, y, w, R);
+    else LAUNCH_IDX(spmv_kernel, (T, double, 1), geo(h), h->A64, x, y, w, R);
   } else {
-    if (two) LAUNCH((spmv_kernel<T, float, 2>), geo(h), (const float*)h->Alo, x, y, w, R);
-    else LAUNCH((spmv_kernel<T, float, 1>), geo(h), (const float*)h->Alo, x, y, w, R);
+    if (two) LAUNCH_IDX(spmv_kernel, (T, float, 2), geo(h), (const float*)h->Alo, x, y, w, R);
+    else LAUNCH_IDX(spmv_kernel, (T, float, 1), geo(h), (const float*)h->Alo, x, y, w, R);
   }
   return NDIAG_OK;
 }
@@ -276,22 +477,22 @@ template <class T>
 ndiag_status spmv_any(Handle* h, const T* x, T* y) {
   Reduce R{};
   if (sizeof(T) == 8)
-    LAUNCH((spmv_kernel<T, double, 0>), geo(h), h->A64, x, y, (const T*)nullptr, R);
+    LAUNCH_IDX(spmv_kernel, (T, double, 0), geo(h), h->A64, x, y, (const T*)nullptr, R);
   else
-    LAUNCH((spmv_kernel<T, float, 0>), geo(h), (const float*)h->Alo, x, y, (const T*)nullptr, R);
+    LAUNCH_IDX(spmv_kernel, (T, float, 0), geo(h), (const float*)h->Alo, x, y, (const T*)nullptr, R);
   return NDIAG_OK;
 }
 
 ndiag_status residual64(Handle* h, const double* b, const double* x, double* r, double* res) {
   Reduce R = reduce_slot(h, 0);
   R.res = res;
-  LAUNCH((residual_kernel<double>), geo(h), h->A64, b, x, r, R);
+  LAUNCH_IDX(residual_kernel, (double), geo(h), h->A64, b, x, r, R);
   return NDIAG_OK;
 }
 ndiag_status residual64_to32(Handle* h, const double* b, const double* x, float* r, double* res) {
   Reduce R = reduce_slot(h, 0);
   R.res = res;
-  LAUNCH((residual_kernel<float>), geo(h), h->A64, b, x, r, R);
+  LAUNCH_IDX(residual_kernel, (float), geo(h), h->A64, b, x, r, R);
   return NDIAG_OK;
 }
 

@@ -18,7 +18,7 @@ enum { RED_SLOTS = 4, RED_RES = 64 };
 enum {
   SC_BASE = 16,
   SC_RHO = SC_BASE, SC_RHO_OLD, SC_ALPHA, SC_OM, SC_RV, SC_TS, SC_TT, SC_SS, SC_RR, SC_RHO_NEXT,
-  SC_RZ, SC_RZ_NEW, SC_PQ, SC_BB, SC_R0, SC_END
+  SC_RZ, SC_RZ_NEW, SC_PQ, SC_BB, SC_R0, SC_TOL2, SC_END
 };
 
 int grid_blocks(const Handle* h);

@@ -104,6 +104,8 @@ ndiag_status bicgstab(Handle* h, const Prec& P, const T* b, T* x, const KV<T>& V
   const double* hs = h->red_host;
   const size_t vb = sizeof(T) * (size_t)h->N;
   int it = 0;
+  h->red_host[SC_TOL2] = tol_abs * tol_abs;  // the device's half-step exit test
+  ND_CUDA(cudaMemcpyAsync(sc + SC_TOL2, h->red_host + SC_TOL2, sizeof(double), cudaMemcpyHostToDevice, h->stream));
   for (;;) {
     ND_TRY(init_residual<T>(h, b, x, V.r, sc + SC_R0, x_is_zero));
     ND_TRY(pull(h));
@@ -112,6 +114,8 @@ ndiag_status bicgstab(Handle* h, const Prec& P, const T* b, T* x, const KV<T>& V
     ND_TRY(dots<T>(h, 1, V.rh, V.r, nullptr, nullptr, nullptr, nullptr, sc + SC_RHO_NEXT, 1));
     bool converged = false;
     int first = 1;
+    // one host read per iteration: the half-step exit is taken on the device
+    // (bicg_xr with om = 0), and is recognised here from ||s||
     while (it < maxit) {
       ++h->launches;
       bicg_scalars_kernel<<<1, 1, 0, h->stream>>>(sc, first);
@@ -121,6 +125,9 @@ ndiag_status bicgstab(Handle* h, const Prec& P, const T* b, T* x, const KV<T>& V
       ND_TRY(apply_prec(h, P, V.p, V.ph, vb));
       ND_TRY(spmv_dot<T>(h, V.ph, V.v, V.rh, sc + SC_RV, 1));
       ND_TRY(bicg_s<T>(h, V.r, V.v, V.s, sc));
+      ND_TRY(apply_prec(h, P, V.s, V.sh, vb));
+      ND_TRY(spmv_dot<T>(h, V.sh, V.t, V.s, sc + SC_TS, 2, true));
+      ND_TRY(bicg_xr<T>(h, x, V.ph, V.sh, V.r, V.s, V.t, V.rh, sc));
       ND_TRY(pull(h));
       if (hs[SC_RHO] == 0.0 || hs[SC_RV] == 0.0 || !std::isfinite(hs[SC_SS])) {
         *iters = it;
@@ -128,15 +135,10 @@ ndiag_status bicgstab(Handle* h, const Prec& P, const T* b, T* x, const KV<T>& V
         return NDIAG_EBREAKDOWN;
       }
       ++it;
-      if (std::sqrt(hs[SC_SS]) <= tol_abs) {
-        ND_TRY(axpy_alpha<T>(h, x, V.ph, sc));
+      if (hs[SC_SS] <= hs[SC_TOL2]) {
         converged = true;
         break;
       }
-      ND_TRY(apply_prec(h, P, V.s, V.sh, vb));
-      ND_TRY(spmv_dot<T>(h, V.sh, V.t, V.s, sc + SC_TS, 2, true));
-      ND_TRY(bicg_xr<T>(h, x, V.ph, V.sh, V.r, V.s, V.t, V.rh, sc));
-      ND_TRY(pull(h));
       if (!std::isfinite(hs[SC_RR])) {
         *iters = it;
         set_error("BiCGSTAB breakdown (non-finite residual)");

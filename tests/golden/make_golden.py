@@ -4,6 +4,7 @@ oracle (oracle/) on the seeded inputs (paper_1008_3699_gb300/workloads.py).
 Nothing here touches the CUDA library. Usage:
     python tests/golden/make_golden.py poisson64   # seconds
     python tests/golden/make_golden.py varcoef2048 # long: two full 2048^2 solves
+    python tests/golden/make_golden.py varcoef2048_envelope  # long: 7 perturbed solves in parallel
 Output: tests/golden/<name>.json
 """
 import json
@@ -47,7 +48,30 @@ def varcoef2048(n=2048, sub=16):
     return out
 
 
-JOBS = {"poisson64": poisson64, "varcoef2048": varcoef2048}
+def _perturbed_solve(k, n=2048, sub=16):
+    """Oracle BiCGSTAB count of the 2048^2 workload with b scaled by
+    (1 + 1e-15 g), g ~ N(0, 1) from seed 4242 + k (rounding-level change)."""
+    import oracle as orc
+    p = W.varcoef2d_problem(n, sub)
+    g = np.random.default_rng(4242 + k)
+    b = p["b"] * (1.0 + 1e-15 * g.standard_normal(p["b"].shape[0]))
+    pb = orc.Problem(2, p["n"], 5, p["diags"], p["sub"])
+    pb.ilu0_factor(orc.DECOMPOSED)
+    _, info = pb.solve(orc.BICGSTAB, orc.PREC_ILU0, orc.DECOMPOSED, 1.0, 1e-8, 20000, b)
+    return dict(k=k, iters=info["iters"], relres=info["relres"])
+
+
+def varcoef2048_envelope(count=7):
+    """Spread of the oracle's decomposed BiCGSTAB count under 1e-15 relative
+    perturbations of b (one process per solve, spawned)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(count) as pool:
+        runs = pool.map(_perturbed_solve, range(count))
+    its = [r["iters"] for r in runs]
+    return dict(perturbation="b * (1 + 1e-15 g), g ~ N(0,1), seeds 4242..", runs=runs, min=min(its), max=max(its))
+
+
+JOBS = {"poisson64": poisson64, "varcoef2048": varcoef2048, "varcoef2048_envelope": varcoef2048_envelope}
 
 if __name__ == "__main__":
     oracle.build()
