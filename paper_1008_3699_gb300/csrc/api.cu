@@ -353,6 +353,9 @@ void ndiag_destroy(ndiag* h) {
   dev_free(h->sor.base, h->sor.bytes, s);
   dev_free(h->ilu.base, h->ilu.bytes, s);
   dev_free(h->sorT.base, h->sorT.bytes, s);
+  dev_free(h->sor.lev, h->sor.lev_bytes, s);
+  dev_free(h->ilu.lev, h->ilu.lev_bytes, s);
+  dev_free(h->sorT.lev, h->sorT.lev_bytes, s);
   dev_free(h->vcount, h->vcount_bytes, s);
   dev_free(h->sync, h->sync_bytes, s);
   dev_free(h->twin_hand, h->twin_hand_bytes, s);

@@ -2,6 +2,8 @@
 // updates, and dot products with a deterministic two-level reduction (fixed
 // grid, fixed order; the last block to finish sums the block partials in
 // index order, so a result does not depend on scheduling).
+#include <initializer_list>
+
 #include "blas.h"
 
 namespace nd {
@@ -129,6 +131,76 @@ __global__ void __launch_bounds__(BT, BPS_STENCIL) spmv_kernel(Geo g, const TA* 
   }
 }
 
+template <class T>
+struct Pair;
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+
+// 2D 5-point y = A x on cell pairs (i, i + 1), i even, nx even: the five
+// diagonals, x, w and y move as pairs; x[i - 1] and x[i + 2] are single loads
+// (L1 hits). ND as in spmv_kernel. Every thread keeps one pair's eleven
+// loads in flight.
+template <class T, int ND>
+__global__ void __launch_bounds__(BT, BPS) spmv5_pair_kernel(int nx, int ny, int64_t N, const T* __restrict__ A,
+                                                             const T* __restrict__ x, T* __restrict__ y,
+                                                             const T* __restrict__ w, Reduce R) {
+  using P2 = typename Pair<T>::type;
+  const int64_t np = N / 2;
+  const unsigned hx = (unsigned)nx / 2;
+  const P2* A2 = reinterpret_cast<const P2*>(A);
+  const P2* x2 = reinterpret_cast<const P2*>(x);
+  const P2* w2 = reinterpret_cast<const P2*>(w);
+  P2* y2 = reinterpret_cast<P2*>(y);
+  const int64_t NP = np;  // pairs per diagonal
+  double d0 = 0.0, d1 = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * BT + threadIdx.x; p < np; p += (int64_t)gridDim.x * BT) {
+    const unsigned row = (unsigned)p / hx;
+    const int cx = 2 * (int)((unsigned)p - row * hx), cy = (int)row;
+    const int64_t i = 2 * p;
+    const P2 a0 = A2[p], aW = A2[NP + p], aE = A2[2 * NP + p], aS = A2[3 * NP + p], aN = A2[4 * NP + p];
+    const P2 xc = x2[p];
+    const bool hw = cx > 0, he = cx + 2 < nx, hs = cy > 0, hn = cy + 1 < ny;
+    const T xw = hw ? x[i - 1] : T(0);
+    const T xe = he ? x[i + 2] : T(0);
+    P2 xs, xn, wv;
+    if (hs) xs = x2[p - hx];
+    if (hn) xn = x2[p + hx];
+    if (ND >= 1) wv = w2[p];
+    T v0 = a0.x * xc.x, v1 = a0.y * xc.y;
+    if (hw) v0 = fma(aW.x, xw, v0);
+    v1 = fma(aW.y, xc.x, v1);
+    v0 = fma(aE.x, xc.y, v0);
+    if (he) v1 = fma(aE.y, xe, v1);
+    if (hs) {
+      v0 = fma(aS.x, xs.x, v0);
+      v1 = fma(aS.y, xs.y, v1);
+    }
+    if (hn) {
+      v0 = fma(aN.x, xn.x, v0);
+      v1 = fma(aN.y, xn.y, v1);
+    }
+    P2 out;
+    out.x = v0;
+    out.y = v1;
+    y2[p] = out;
+    if (ND >= 1) d0 += (double)wv.x * (double)v0 + (double)wv.y * (double)v1;
+    if (ND >= 2) d1 += (double)v0 * (double)v0 + (double)v1 * (double)v1;
+  }
+  if (ND == 1) {
+    double vv[1] = {d0};
+    finish_reduce<1>(vv, R);
+  } else if (ND == 2) {
+    double vv[2] = {d0, d1};
+    finish_reduce<2>(vv, R);
+  }
+}
+
 // r = b - A x (fp64), ||r||^2
 template <class TB, class IDX>
 __global__ void __launch_bounds__(BT, BPS_STENCIL) residual_kernel(Geo g, const double* __restrict__ A,
@@ -166,7 +238,7 @@ __global__ void __launch_bounds__(BT, BPS) dots_kernel(int64_t N, const T* __res
                                                        const T* __restrict__ b2, Reduce R) {
   double d[NV];
   for (int k = 0; k < NV; ++k) d[k] = 0.0;
-  constexpr int U = NV > 2 ? 2 : 4;
+  constexpr int U = NV > 2 ? 3 : (NV > 1 ? 4 : 8);
   ND_STREAM_LOOP(N) {
     T va[NV][U], vb[NV][U];
 #pragma unroll
@@ -193,6 +265,7 @@ __global__ void __launch_bounds__(BT, BPS) bicg_p_kernel(int64_t N, const T* __r
                                                          const T* __restrict__ v, const double* sc, int first) {
   const double rho = sc[SC_RHO], rho_old = sc[SC_RHO_OLD], alpha = sc[SC_ALPHA], om = sc[SC_OM];
   const double beta = first ? 0.0 : (rho / rho_old) * (alpha / om);
+  constexpr int U = 6;  // three streams in
   ND_STREAM_LOOP(N) {
     T vr[U], vp[U], vv[U];
 #pragma unroll
@@ -217,6 +290,7 @@ __global__ void __launch_bounds__(BT, BPS) bicg_s_kernel(int64_t N, const T* __r
                                                          const double* sc, Reduce R) {
   const double alpha = sc[SC_RHO] / sc[SC_RV];
   double d = 0.0;
+  constexpr int U = 8;  // two streams in
   ND_STREAM_LOOP(N) {
     T vr[U], vv[U];
 #pragma unroll
@@ -304,7 +378,7 @@ __global__ void __launch_bounds__(BT, BPS) cg_xr_kernel(int64_t N, T* __restrict
                                                         const double* sc, Reduce R) {
   const double alpha = sc[SC_RZ] / sc[SC_PQ];
   double d = 0.0;
-  constexpr int U = 3;  // four streams
+  constexpr int U = 4;  // four streams
   ND_STREAM_LOOP(N) {
     T vx[U], vp[U], vr[U], vq[U];
 #pragma unroll
@@ -331,6 +405,7 @@ template <class T>
 __global__ void __launch_bounds__(BT, BPS) cg_p_kernel(int64_t N, const T* __restrict__ z, T* __restrict__ p,
                                                        const double* sc, int first) {
   const double beta = first ? 0.0 : sc[SC_RZ_NEW] / sc[SC_RZ];
+  constexpr int U = 8;  // two streams in
   ND_STREAM_LOOP(N) {
     T vz[U], vp[U];
 #pragma unroll
@@ -460,10 +535,26 @@ ndiag_status spmv64(Handle* h, const double* x, double* y) {
   return NDIAG_OK;
 }
 
+// 2D 5-point grids with even nx and pair-aligned vectors take the pair kernel
+template <class T>
+bool pair_ok(const Handle* h, const void* A, std::initializer_list<const void*> v) {
+  if (h->stencil != 5 || h->n[2] != 1 || (h->n[0] & 1) || !small_index(h)) return false;
+  if ((uintptr_t)A % (2 * sizeof(T))) return false;
+  for (const void* p : v)
+    if (p && (uintptr_t)p % (2 * sizeof(T))) return false;
+  return true;
+}
+
 template <class T>
 ndiag_status spmv_dot(Handle* h, const T* x, T* y, const T* w, double* res, int slot, bool two) {
   Reduce R = reduce_slot(h, slot);
   R.res = res;
+  const T* A = sizeof(T) == 8 ? (const T*)h->A64 : (const T*)h->Alo;
+  if (pair_ok<T>(h, A, {x, y, w})) {
+    if (two) LAUNCH((spmv5_pair_kernel<T, 2>), (int)h->n[0], (int)h->n[1], h->N, A, x, y, w, R);
+    else LAUNCH((spmv5_pair_kernel<T, 1>), (int)h->n[0], (int)h->n[1], h->N, A, x, y, w, R);
+    return NDIAG_OK;
+  }
   if (sizeof(T) == 8) {
     if (two) LAUNCH_IDX(spmv_kernel, (T, double, 2), geo(h), h->A64, x, y, w, R);
     else LAUNCH_IDX(spmv_kernel, (T, double, 1), geo(h), h->A64, x, y, w, R);

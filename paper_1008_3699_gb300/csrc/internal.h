@@ -54,6 +54,10 @@ struct ScaledSet {
   void* base = nullptr;  // one allocation: s arrays of N values (inv, then entries 1..s-1)
   size_t bytes = 0;
   unsigned version = 0;  // bumped whenever the values change (invalidates line tables)
+  // 3D: the same arrays in level order (built on first use by the pencil sweeps)
+  void* lev = nullptr;
+  size_t lev_bytes = 0;
+  unsigned lev_version = ~0u;
 };
 
 // Coefficients of the coupled start lines of one sweep phase (2D): for every
@@ -141,6 +145,11 @@ struct Split {
   __host__ __device__ int lo(int k) const { return k * q + (k < r ? k : r); }
   __host__ __device__ int len(int k) const { return q + (k < r ? 1 : 0); }
 };
+// part holding coordinate x
+__host__ __device__ inline int split_find(const Split& s, int x) {
+  const int big = s.r * (s.q + 1);
+  return x < big ? x / (s.q + 1) : s.r + (x - big) / s.q;
+}
 
 // Start corner of subdomain 0 at phase t (Sec. 2 step (ii); Sec. 3 "Sweeping
 // directions"; Sec. 4): 1D alternates starting left-to-right; in 2D/3D the

@@ -155,11 +155,6 @@ struct Geo {
   __host__ __device__ int gyl(int ly) const { return cy ? gy0 + h - 1 - ly : gy0 + ly; }
 };
 
-__host__ __device__ inline int split_find(const Split& s, int x) {
-  const int big = s.r * (s.q + 1);
-  return x < big ? x / (s.q + 1) : s.r + (x - big) / s.q;
-}
-
 // Geometry of subdomain (ix, iy) at the launch's phase.
 template <class T, class TC>
 __host__ __device__ inline Geo subdomain_geo(const StagedP<T, TC>& P, int ix, int iy, bool& tx, bool& ty) {

@@ -38,7 +38,7 @@ using namespace sweep;
 
 constexpr int GT = 256;  // threads per CTA
 
-enum { REG_ALL = 0, REG_INTERIOR = 1, REG_FACES = 2, REG_EDGES = 3, REG_CORNERS = 4 };
+enum { REG_ALL = 0, REG_INTERIOR = 1, REG_FACES = 2, REG_EDGES = 3, REG_CORNERS = 4, REG_BLOCKS = 5 };
 
 template <class T, class TC>
 struct GP {
@@ -58,6 +58,14 @@ struct GP {
   T om[8];  // relaxation per start corner
   T bscale;
   DevStatus* st;
+  int twin_slots;  // elements of the twin store
+  // level-ordered copy of the scaled set (or null): array k of subdomain s at
+  // level L and row q = y + h0 z of the reference frame is
+  // lev[k * lev_arr + s * lev_sub + L * lev_hd0 + q]; lev_flip = axes on which
+  // this launch's frame is the reference frame reversed
+  const TC* lev;
+  int64_t lev_arr, lev_sub;
+  int lev_h0, lev_hd0, lev_flip;
 };
 
 struct Sub {
@@ -134,8 +142,179 @@ __device__ __forceinline__ bool in_region(int region, int C) {
     case REG_FACES: return k == 1;
     case REG_EDGES: return k == 2;
     case REG_CORNERS: return k == 3;
+    case REG_BLOCKS: return k > 0;
     default: return true;
   }
+}
+
+// One coupled block: the own cell (x, y, z) lies at 0 on the NC coupled axes C.
+// Solves the block, stores the own member to xnew and the twins to the twin
+// store, and returns the own member's value.
+template <class T, class TC, int KIND, bool OM1, int NC>
+__device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const TwinIdx& TI, T* tw, int x, int y,
+                                      int z, int C, int tcode) {
+  const int own[3] = {x, y, z};
+  // canonical member order: bit r of a member index <-> r-th coupled axis,
+  // set when the member has the larger global coordinate along it
+  int axes[3], nC = 0;
+  for (int a = 0; a < 3; ++a)
+    if (C >> a & 1) axes[nC++] = a;
+  constexpr int n = 1 << NC;  // nC == NC
+  int mo = 0;  // own member
+  for (int r = 0; r < nC; ++r)
+    if (S.c[axes[r]] == 0) mo |= 1 << r;
+  T M[n][n], hv[n];
+  int64_t gidx[n];
+#pragma unroll
+  for (int m = 0; m < n; ++m) {
+    int lc[3] = {own[0], own[1], own[2]}, sub = 0;
+    for (int r = 0; r < nC; ++r)
+      if (((m ^ mo) >> r) & 1) {
+        lc[axes[r]] = -1;
+        sub |= 1 << axes[r];
+      }
+    int cm[3];
+    for (int a = 0; a < 3; ++a) cm[a] = S.c[a] ^ ((sub >> a) & 1);
+    int64_t gi = 0;
+    int gc[3];
+    for (int a = 0; a < 3; ++a) {
+      gc[a] = S.gco(a, lc[a]);
+      gi += (int64_t)gc[a] * P.stride[a];
+    }
+    gidx[m] = gi;
+    const T om = OM1 ? T(1) : P.om[cm[0] | (cm[1] << 1) | (cm[2] << 2)];
+#pragma unroll
+    for (int k = 0; k < n; ++k) M[m][k] = T(0);
+    M[m][m] = T(1);
+    T acc;
+    if (!P.transposed) {
+      if (KIND == KIND_SOR) {
+        T e = ldco<T, TC>(P.inv + gi) * __ldg(P.rhs + gi);
+        for (int a = 0; a < P.dim; ++a) {
+          const int dn = cm[a] ? 0 : 1;  // downstream side of the member along a
+          const int gd = gc[a] + (dn ? 1 : -1);
+          if (gd >= 0 && gd < P.n[a])
+            e = fma(-ldco<T, TC>(P.c[ent(a, dn)] + gi), __ldg(P.xold + gi + (dn ? P.stride[a] : -P.stride[a])), e);
+          const bool implicit_up = (C >> a & 1) || lc[a] >= 1;
+          const int gu = gc[a] + (dn ? -1 : 1);
+          if (!implicit_up && gu >= 0 && gu < P.n[a])
+            e = fma(-ldco<T, TC>(P.c[ent(a, 1 - dn)] + gi), __ldg(P.xold + gi + (dn ? -P.stride[a] : P.stride[a])), e);
+        }
+        acc = OM1 ? e : fma(om, e, (T(1) - om) * __ldg(P.xold + gi));
+      } else if (KIND == KIND_TRI_SCALED) {
+        acc = ldco<T, TC>(P.inv + gi) * __ldg(P.rhs + gi);
+        if (!OM1) acc *= P.bscale;
+      } else {
+        acc = __ldg(P.rhs + gi);
+      }
+      // upstream neighbours: block partners, or earlier blocks' members
+      for (int a = 0; a < P.dim; ++a) {
+        const int up = cm[a] ? 1 : 0;  // upstream side of the member along a
+        if (C >> a & 1) {
+          int r = 0;
+          while (axes[r] != a) ++r;
+          T g = ldco<T, TC>(P.c[ent(a, up)] + gi);
+          if (!OM1) g *= om;
+          M[m][m ^ (1 << r)] = g;
+        } else if (lc[a] >= 1) {
+          T g = ldco<T, TC>(P.c[ent(a, up)] + gi);
+          if (!OM1) g *= om;
+          const int64_t gp = gi + (up ? P.stride[a] : -P.stride[a]);
+          T v;
+          if (sub == 0) {
+            v = __ldcg(P.xnew + gp);
+          } else {
+            int pc[3] = {lc[0], lc[1], lc[2]};
+            pc[a] -= 1;
+            v = tw[TI.slot(sub, pc)];
+          }
+          acc = fma(-g, v, acc);
+        }
+      }
+    } else {
+      // transposed: dependents are the downstream neighbours inside the
+      // member's own subdomain, and the block partners
+      acc = __ldg(P.rhs + gi);
+      for (int a = 0; a < P.dim; ++a) {
+        const int up = cm[a] ? 1 : 0, dn = 1 - up;
+        if (C >> a & 1) {
+          int r = 0;
+          while (axes[r] != a) ++r;
+          T g = ldco<T, TC>(P.c[ent(a, up)] + gi);
+          if (!OM1) g *= om;
+          M[m][m ^ (1 << r)] = g;
+        }
+        // downstream neighbour inside the member's subdomain: local
+        // coordinate +1 (own side), or -2 (twin side along a)
+        const bool twin_axis = (sub >> a) & 1;
+        const int gd = gc[a] + (dn ? 1 : -1);
+        bool inside;
+        if (twin_axis) {  // the twin's subdomain: the neighbour across S's start face
+          const int it = S.c[a] ? S.idx[a] + 1 : S.idx[a] - 1;
+          const int t0 = P.sp[a].lo(it), t1 = t0 + P.sp[a].len(it);
+          inside = gd >= t0 && gd < t1;
+        } else {
+          inside = lc[a] + 1 < S.len[a];
+        }
+        if (!inside) continue;
+        T g = ldco<T, TC>(P.c[ent(a, dn)] + gi);
+        if (!OM1) g *= om;
+        const int64_t gq = gi + (dn ? P.stride[a] : -P.stride[a]);
+        T v;
+        if (sub == 0 || twin_axis) {
+          v = __ldcg(P.xnew + gq);
+        } else {
+          // same twin subset one step downstream: this launch's store
+          // if that block is of the same kind, else an earlier launch
+          int pc[3] = {lc[0], lc[1], lc[2]};
+          pc[a] += 1;
+          int oc[3] = {own[0], own[1], own[2]};
+          oc[a] += 1;
+          const int C2 = ((oc[0] == 0) | ((oc[1] == 0) << 1) | ((oc[2] == 0) << 2)) & tcode;
+          v = (__popc(C2) == nC) ? tw[TI.slot(sub, pc)] : __ldcg(P.xnew + gq);
+        }
+        acc = fma(-g, v, acc);
+      }
+    }
+    hv[m] = acc;
+  }
+  // (I + G) x = h, elimination in canonical order (diagonally dominant: no pivoting)
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    const T piv = M[k][k];
+#pragma unroll
+    for (int i = k + 1; i < n; ++i) {
+      const T f = M[i][k] / piv;
+      if (f != T(0)) {
+#pragma unroll
+        for (int j = k + 1; j < n; ++j) M[i][j] = fma(-f, M[k][j], M[i][j]);
+        hv[i] = fma(-f, hv[k], hv[i]);
+      }
+    }
+  }
+  T xs[n];
+#pragma unroll
+  for (int k = n - 1; k >= 0; --k) {
+    T s = hv[k];
+#pragma unroll
+    for (int j = k + 1; j < n; ++j) s = fma(-M[k][j], xs[j], s);
+    xs[k] = s / M[k][k];
+  }
+#pragma unroll
+  for (int m = 0; m < n; ++m) {
+    if (m == mo) {
+      P.xnew[gidx[m]] = xs[m];
+    } else {
+      int lc[3] = {own[0], own[1], own[2]}, sub = 0;
+      for (int r = 0; r < nC; ++r)
+        if (((m ^ mo) >> r) & 1) {
+          lc[axes[r]] = -1;
+          sub |= 1 << axes[r];
+        }
+      tw[TI.slot(sub, lc)] = xs[m];
+    }
+  }
+  return xs[mo];
 }
 
 template <class T, class TC, int KIND, bool OM1>
@@ -147,11 +326,37 @@ __global__ void __launch_bounds__(GT) sweep3d_kernel(GP<T, TC> P) {
   const TwinIdx TI = twin_index(w, h, d);
   const int lmax = (w - 1) + (h - 1) + (d - 1);
   const int tcode = S.t[0] | (S.t[1] << 1) | (S.t[2] << 2);
+  const bool blocks_only = P.region != REG_ALL && P.region != REG_INTERIOR;
+  const int umax = max(w, max(h, d));
   for (int it = 0; it <= lmax; ++it) {
     const int L = P.transposed ? lmax - it : it;
-    for (int q = threadIdx.x; q < h * d; q += GT) {
-      const int y = q % h, z = q / h, x = L - y - z;
-      if (x < 0 || x >= w) continue;
+    // REG_ALL / REG_INTERIOR: every row (y, z) meets its cell x = L - y - z.
+    // Block regions: only cells with a zero coordinate can be blocks; cell c
+    // of a level enumerates face a = c / umax (coordinate a = 0), the cell
+    // taken on the first face where it has a zero coordinate.
+    const int nq = blocks_only ? 3 * umax : h * d;
+    for (int q = threadIdx.x; q < nq; q += GT) {
+      int x, y, z;
+      if (!blocks_only) {
+        y = q % h;
+        z = q / h;
+        x = L - y - z;
+        if (x < 0 || x >= w) continue;
+      } else {
+        const int a = q / umax, u = q - a * umax;
+        const int lu = a == 0 ? h : w, lv = a == 2 ? h : d;
+        const int v = L - u;
+        if (u >= lu || v < 0 || v >= lv) continue;
+        if (a == 0) {
+          x = 0, y = u, z = v;
+        } else if (a == 1) {
+          x = u, y = 0, z = v;
+          if (x == 0) continue;
+        } else {
+          x = u, y = v, z = 0;
+          if (x == 0 || y == 0) continue;
+        }
+      }
       const int own[3] = {x, y, z};
       const int C = ((x == 0) | ((y == 0) << 1) | ((z == 0) << 2)) & tcode;
       if (!in_region(P.region, C)) continue;
@@ -203,158 +408,151 @@ __global__ void __launch_bounds__(GT) sweep3d_kernel(GP<T, TC> P) {
         P.xnew[gi] = acc;
         continue;
       }
-      // canonical member order: bit r of a member index <-> r-th coupled axis,
-      // set when the member has the larger global coordinate along it
-      int axes[3], nC = 0;
-      for (int a = 0; a < 3; ++a)
-        if (C >> a & 1) axes[nC++] = a;
-      const int n = 1 << nC;
-      int mo = 0;  // own member
-      for (int r = 0; r < nC; ++r)
-        if (S.c[axes[r]] == 0) mo |= 1 << r;
-      T M[8][8], hv[8];
-      int64_t gidx[8];
-      for (int m = 0; m < n; ++m) {
-        int lc[3] = {own[0], own[1], own[2]}, sub = 0;
-        for (int r = 0; r < nC; ++r)
-          if (((m ^ mo) >> r) & 1) {
-            lc[axes[r]] = -1;
-            sub |= 1 << axes[r];
-          }
-        int cm[3];
-        for (int a = 0; a < 3; ++a) cm[a] = S.c[a] ^ ((sub >> a) & 1);
-        int64_t gi = 0;
-        int gc[3];
-        for (int a = 0; a < 3; ++a) {
-          gc[a] = S.gco(a, lc[a]);
-          gi += (int64_t)gc[a] * P.stride[a];
+      if (__popc(C) == 1) block_solve<T, TC, KIND, OM1, 1>(P, S, TI, tw, x, y, z, C, tcode);
+      else if (__popc(C) == 2) block_solve<T, TC, KIND, OM1, 2>(P, S, TI, tw, x, y, z, C, tcode);
+      else block_solve<T, TC, KIND, OM1, 3>(P, S, TI, tw, x, y, z, C, tcode);
+    }
+    __syncthreads();
+  }
+}
+
+// Pencil form of the level walk over the cells of one-cell blocks (C = 0) for
+// the triangular kinds (ILU(0) forward and backward, the SSOR forward half,
+// and the interior pass of the transposed solve). Thread t owns the rows
+// q = t + GT k, i.e. (y, z) = (q mod h, q / h), and meets each row's next cell
+// on every level, so
+//  * the row's previous cell (x - 1, or x + 1 when transposed) is in a register,
+//  * the neighbours along y and z were put into a shared two-level buffer on
+//    the level before,
+//  * every operand of the next level's cells is loaded before this level's
+//    arithmetic starts (one level of prefetch).
+// In a forward pass the coupled blocks on the start faces depend only on each
+// other, so an earlier launch (sweep3d_kernel over REG_BLOCKS) solves them;
+// here their own-cell values are read back from xnew like operands. The
+// arithmetic of a cell is the same, operation for operation, as in
+// sweep3d_kernel.
+constexpr int KR = 4;  // rows per thread: h * d <= KR * GT
+
+template <class T, class TC, int KIND, bool OM1>
+__global__ void __launch_bounds__(GT, 4) sweep3d_pencil_kernel(GP<T, TC> P) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  T* lv = reinterpret_cast<T*>(gsm);  // [2][hd]: the values of the last two levels, by row
+  const Sub S = subdomain(P, blockIdx.x);
+  const int w = S.len[0], h = S.len[1], d = S.len[2], hd = h * d;
+  const int lmax = (w - 1) + (h - 1) + (d - 1);
+  const int tcode = S.t[0] | (S.t[1] << 1) | (S.t[2] << 2);
+  const bool tr = P.transposed != 0;
+  const T om = OM1 ? T(1) : P.om[S.c[0] | (S.c[1] << 1) | (S.c[2] << 2)];
+  int yk[KR], zk[KR];
+#pragma unroll
+  for (int k = 0; k < KR; ++k) {
+    const int q = threadIdx.x + GT * k;
+    yk[k] = q < hd ? q % h : 0;
+    zk[k] = q < hd ? q / h : 0;
+  }
+  // global index of the row's cell at local x
+  auto gidx = [&](int k, int x) -> int64_t {
+    return (int64_t)S.gco(0, x) + (int64_t)S.gco(1, yk[k]) * P.stride[1] + (int64_t)S.gco(2, zk[k]) * P.stride[2];
+  };
+  // raw operands of each row's cell on the coming level: inv, rhs, and the
+  // couplings along x, y, z (0 where the neighbour is absent)
+  T pi[KR], pr[KR], pg[KR][3];
+  auto fetch = [&](int L) {
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      const int q = threadIdx.x + GT * k;
+      const int x = L - yk[k] - zk[k];
+      if (q >= hd || x < 0 || x >= w) continue;
+      const int C = ((x == 0) | ((yk[k] == 0) << 1) | ((zk[k] == 0) << 2)) & tcode;
+      const int64_t gi = gidx(k, x);
+      if (C != 0) {  // solved by the block launch (forward passes only)
+        if (!tr) pr[k] = __ldcg(P.xnew + gi);
+        continue;
+      }
+      const int own[3] = {x, yk[k], zk[k]};
+      // coefficient k of this cell: the level-ordered copy (consecutive rows
+      // at consecutive addresses) or the natural arrays
+      const TC* cbase;
+      int64_t ci;
+      if (P.lev) {
+        const int xr = (P.lev_flip & 1) ? w - 1 - x : x;
+        const int yr = (P.lev_flip & 2) ? h - 1 - yk[k] : yk[k];
+        const int zr = (P.lev_flip & 4) ? d - 1 - zk[k] : zk[k];
+        cbase = P.lev + (int64_t)blockIdx.x * P.lev_sub;
+        ci = (int64_t)(xr + yr + zr) * P.lev_hd0 + yr + P.lev_h0 * zr;
+      } else {
+        cbase = P.inv;
+        ci = gi;
+      }
+      const int64_t ca = P.lev ? P.lev_arr : (int64_t)(P.c[0] - P.inv);
+      if (!tr && KIND == KIND_TRI_SCALED) pi[k] = ldco<T, TC>(cbase + ci);
+      pr[k] = __ldg(P.rhs + gi);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (!tr) {
+          const int up = S.c[a] ? 1 : 0;
+          pg[k][a] = own[a] >= 1 ? ldco<T, TC>(cbase + (1 + ent(a, up)) * ca + ci) : T(0);
+        } else {
+          const int dn = S.c[a] ? 0 : 1;
+          pg[k][a] = own[a] + 1 < S.len[a] ? ldco<T, TC>(cbase + (1 + ent(a, dn)) * ca + ci) : T(0);
         }
-        gidx[m] = gi;
-        const T om = OM1 ? T(1) : P.om[cm[0] | (cm[1] << 1) | (cm[2] << 2)];
-        for (int k = 0; k < n; ++k) M[m][k] = T(0);
-        M[m][m] = T(1);
+      }
+    }
+  };
+  T xr[KR];
+#pragma unroll
+  for (int k = 0; k < KR; ++k) xr[k] = T(0);
+  fetch(tr ? lmax : 0);
+  for (int it = 0; it <= lmax; ++it) {
+    const int L = tr ? lmax - it : it;
+    const int cur = it & 1, prv = cur ^ 1;
+    T ci[KR], cr[KR], cg[KR][3];
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      ci[k] = pi[k];
+      cr[k] = pr[k];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) cg[k][a] = pg[k][a];
+    }
+    if (it < lmax) fetch(tr ? L - 1 : L + 1);
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      const int q = threadIdx.x + GT * k;
+      const int x = L - yk[k] - zk[k];
+      if (q >= hd || x < 0 || x >= w) continue;
+      const int C = ((x == 0) | ((yk[k] == 0) << 1) | ((zk[k] == 0) << 2)) & tcode;
+      if (C != 0 && tr) continue;  // the transposed block passes follow this one
+      T v;
+      if (C != 0) {
+        v = cr[k];
+      } else {
         T acc;
-        if (!P.transposed) {
-          if (KIND == KIND_SOR) {
-            T e = ldco<T, TC>(P.inv + gi) * __ldg(P.rhs + gi);
-            for (int a = 0; a < P.dim; ++a) {
-              const int dn = cm[a] ? 0 : 1;  // downstream side of the member along a
-              const int gd = gc[a] + (dn ? 1 : -1);
-              if (gd >= 0 && gd < P.n[a])
-                e = fma(-ldco<T, TC>(P.c[ent(a, dn)] + gi), __ldg(P.xold + gi + (dn ? P.stride[a] : -P.stride[a])), e);
-              const bool implicit_up = (C >> a & 1) || lc[a] >= 1;
-              const int gu = gc[a] + (dn ? -1 : 1);
-              if (!implicit_up && gu >= 0 && gu < P.n[a])
-                e = fma(-ldco<T, TC>(P.c[ent(a, 1 - dn)] + gi), __ldg(P.xold + gi + (dn ? -P.stride[a] : P.stride[a])), e);
-            }
-            acc = OM1 ? e : fma(om, e, (T(1) - om) * __ldg(P.xold + gi));
-          } else if (KIND == KIND_TRI_SCALED) {
-            acc = ldco<T, TC>(P.inv + gi) * __ldg(P.rhs + gi);
-            if (!OM1) acc *= P.bscale;
-          } else {
-            acc = __ldg(P.rhs + gi);
-          }
-          // upstream neighbours: block partners, or earlier blocks' members
-          for (int a = 0; a < P.dim; ++a) {
-            const int up = cm[a] ? 1 : 0;  // upstream side of the member along a
-            if (C >> a & 1) {
-              int r = 0;
-              while (axes[r] != a) ++r;
-              T g = ldco<T, TC>(P.c[ent(a, up)] + gi);
-              if (!OM1) g *= om;
-              M[m][m ^ (1 << r)] = g;
-            } else if (lc[a] >= 1) {
-              T g = ldco<T, TC>(P.c[ent(a, up)] + gi);
-              if (!OM1) g *= om;
-              const int64_t gp = gi + (up ? P.stride[a] : -P.stride[a]);
-              T v;
-              if (sub == 0) {
-                v = __ldcg(P.xnew + gp);
-              } else {
-                int pc[3] = {lc[0], lc[1], lc[2]};
-                pc[a] -= 1;
-                v = tw[TI.slot(sub, pc)];
-              }
-              acc = fma(-g, v, acc);
-            }
-          }
+        if (!tr && KIND == KIND_TRI_SCALED) {
+          acc = ci[k] * cr[k];
+          if (!OM1) acc *= P.bscale;
         } else {
-          // transposed: dependents are the downstream neighbours inside the
-          // member's own subdomain, and the block partners
-          acc = __ldg(P.rhs + gi);
-          for (int a = 0; a < P.dim; ++a) {
-            const int up = cm[a] ? 1 : 0, dn = 1 - up;
-            if (C >> a & 1) {
-              int r = 0;
-              while (axes[r] != a) ++r;
-              T g = ldco<T, TC>(P.c[ent(a, up)] + gi);
-              if (!OM1) g *= om;
-              M[m][m ^ (1 << r)] = g;
-            }
-            // downstream neighbour inside the member's subdomain: local
-            // coordinate +1 (own side), or -2 (twin side along a)
-            const bool twin_axis = (sub >> a) & 1;
-            const int gd = gc[a] + (dn ? 1 : -1);
-            bool inside;
-            if (twin_axis) {  // the twin's subdomain: the neighbour across S's start face
-              const int it = S.c[a] ? S.idx[a] + 1 : S.idx[a] - 1;
-              const int t0 = P.sp[a].lo(it), t1 = t0 + P.sp[a].len(it);
-              inside = gd >= t0 && gd < t1;
-            } else {
-              inside = lc[a] + 1 < S.len[a];
-            }
-            if (!inside) continue;
-            T g = ldco<T, TC>(P.c[ent(a, dn)] + gi);
-            if (!OM1) g *= om;
-            const int64_t gq = gi + (dn ? P.stride[a] : -P.stride[a]);
-            T v;
-            if (sub == 0 || twin_axis) {
-              v = __ldcg(P.xnew + gq);
-            } else {
-              // same twin subset one step downstream: this launch's store
-              // if that block is of the same kind, else an earlier launch
-              int pc[3] = {lc[0], lc[1], lc[2]};
-              pc[a] += 1;
-              int oc[3] = {own[0], own[1], own[2]};
-              oc[a] += 1;
-              const int C2 = ((oc[0] == 0) | ((oc[1] == 0) << 1) | ((oc[2] == 0) << 2)) & tcode;
-              v = (__popc(C2) == nC) ? tw[TI.slot(sub, pc)] : __ldcg(P.xnew + gq);
-            }
-            acc = fma(-g, v, acc);
-          }
+          acc = cr[k];
         }
-        hv[m] = acc;
-      }
-      // (I + G) x = h, elimination in canonical order (diagonally dominant: no pivoting)
-      for (int k = 0; k < n; ++k) {
-        const T piv = M[k][k];
-        for (int i = k + 1; i < n; ++i) {
-          const T f = M[i][k] / piv;
-          if (f != T(0)) {
-            for (int j = k + 1; j < n; ++j) M[i][j] = fma(-f, M[k][j], M[i][j]);
-            hv[i] = fma(-f, hv[k], hv[i]);
-          }
+        T g0 = cg[k][0], g1 = cg[k][1], g2 = cg[k][2];
+        if (!OM1) {
+          g0 *= om;
+          g1 *= om;
+          g2 *= om;
         }
-      }
-      T xs[8];
-      for (int k = n - 1; k >= 0; --k) {
-        T s = hv[k];
-        for (int j = k + 1; j < n; ++j) s = fma(-M[k][j], xs[j], s);
-        xs[k] = s / M[k][k];
-      }
-      for (int m = 0; m < n; ++m) {
-        if (m == mo) {
-          P.xnew[gidx[m]] = xs[m];
+        if (!tr) {
+          if (x >= 1) acc = fma(-g0, xr[k], acc);
+          if (yk[k] >= 1) acc = fma(-g1, lv[prv * hd + q - 1], acc);
+          if (zk[k] >= 1) acc = fma(-g2, lv[prv * hd + q - h], acc);
         } else {
-          int lc[3] = {own[0], own[1], own[2]}, sub = 0;
-          for (int r = 0; r < nC; ++r)
-            if (((m ^ mo) >> r) & 1) {
-              lc[axes[r]] = -1;
-              sub |= 1 << axes[r];
-            }
-          tw[TI.slot(sub, lc)] = xs[m];
+          if (x + 1 < w) acc = fma(-g0, xr[k], acc);
+          if (yk[k] + 1 < h) acc = fma(-g1, lv[prv * hd + q + 1], acc);
+          if (zk[k] + 1 < d) acc = fma(-g2, lv[prv * hd + q + h], acc);
         }
+        P.xnew[gidx(k, x)] = acc;
+        v = acc;
       }
+      lv[cur * hd + q] = v;
+      xr[k] = v;
     }
     __syncthreads();
   }
@@ -390,19 +588,89 @@ __global__ void __launch_bounds__(GT) factor3d_kernel(GP<T, TC> P, const double*
 }
 
 template <class T, class TC, int KIND, bool OM1>
-ndiag_status run3d(Handle* h, const GP<T, TC>& P, unsigned nsub, size_t smem, double bytes) {
+ndiag_status run3d(Handle* h, const GP<T, TC>& P, unsigned nsub, size_t smem, double bytes, bool pencil) {
   static bool attr = false;
   if (!attr) {
     ND_CUDA(cudaFuncSetAttribute(sweep3d_kernel<T, TC, KIND, OM1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024));
     attr = true;
   }
-  const int slot = prof_begin(h);
+  const int slot = bytes > 0 ? prof_begin(h) : -1;
   ++h->launches;
-  ++h->sweep_launches;
+  if (bytes > 0) ++h->sweep_launches;
+  if constexpr (KIND != KIND_SOR) {
+    if (pencil) {
+      sweep3d_pencil_kernel<T, TC, KIND, OM1><<<nsub, GT, 2 * sizeof(T) * (size_t)pencil_rows(P), h->stream>>>(P);
+      ND_CUDA(cudaGetLastError());
+      prof_end(h, slot, bytes);
+      return NDIAG_OK;
+    }
+  }
   sweep3d_kernel<T, TC, KIND, OM1><<<nsub, GT, smem, h->stream>>>(P);
   ND_CUDA(cudaGetLastError());
   prof_end(h, slot, bytes);
+  return NDIAG_OK;
+}
+
+// rows (h * d) of the largest subdomain
+template <class T, class TC>
+int pencil_rows(const GP<T, TC>& P) {
+  return P.sp[1].len(0) * P.sp[2].len(0);
+}
+
+// Level-ordered copy of a scaled set (7 arrays) in the frame of P (the
+// reference frame): one thread per cell.
+template <class T, class TC>
+__global__ void level_layout_kernel(GP<T, TC> P, const TC* src, TC* dst, int64_t N) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int gx = (int)(i % P.n[0]);
+    const int64_t rest = i / P.n[0];
+    const int gy = (int)(rest % P.n[1]), gz = (int)(rest / P.n[1]);
+    const int ix = split_find(P.sp[0], gx), iy = split_find(P.sp[1], gy), iz = split_find(P.sp[2], gz);
+    const unsigned b = (unsigned)(ix + P.sp[0].p * (iy + P.sp[1].p * iz));
+    const Sub S = subdomain(P, b);
+    int l[3];
+    const int g[3] = {gx, gy, gz};
+    for (int a = 0; a < 3; ++a) l[a] = S.c[a] ? S.g0[a] + S.len[a] - 1 - g[a] : g[a] - S.g0[a];
+    const int64_t o = (int64_t)b * P.lev_sub + (int64_t)(l[0] + l[1] + l[2]) * P.lev_hd0 + l[1] + P.lev_h0 * l[2];
+    for (int k = 0; k < 7; ++k) dst[k * P.lev_arr + o] = src[(int64_t)k * N + i];
+  }
+}
+
+// The level-ordered copy of `set` in the frame of the forward phase, built
+// when missing or stale; fills the lev fields of P (null when not applicable).
+template <class T, class TC>
+ndiag_status attach_levels(Handle* h, ScaledSet& set, GP<T, TC>& P, int mode) {
+  P.lev = nullptr;
+  if (mode != NDIAG_DECOMPOSED || h->dim != 3) return NDIAG_OK;
+  GP<T, TC> R = P;  // reference frame: the forward phase
+  R.base = base_corner(3, fwd_phase(3));
+  const int w0 = P.sp[0].len(0), h0 = P.sp[1].len(0), d0 = P.sp[2].len(0);
+  R.lev_h0 = h0;
+  R.lev_hd0 = h0 * d0;
+  R.lev_sub = (int64_t)(w0 + h0 + d0 - 2) * R.lev_hd0;
+  const int64_t nsub = (int64_t)P.sp[0].p * P.sp[1].p * P.sp[2].p;
+  R.lev_arr = nsub * R.lev_sub;
+  const size_t bytes = sizeof(TC) * 7 * (size_t)R.lev_arr;
+  if (!set.lev || set.lev_bytes != bytes) {
+    dev_free(set.lev, set.lev_bytes, h->stream);
+    set.lev = dev_alloc(bytes, h->stream);
+    set.lev_bytes = set.lev ? bytes : 0;
+    set.lev_version = ~0u;
+    if (!set.lev) return NDIAG_OK;  // no room: the natural arrays serve
+  }
+  if (set.lev_version != set.version) {
+    ++h->launches;
+    level_layout_kernel<T, TC><<<h->sm_count * 8, 256, 0, h->stream>>>(R, (const TC*)set.base, (TC*)set.lev, h->N);
+    ND_CUDA(cudaGetLastError());
+    set.lev_version = set.version;
+  }
+  P.lev = (const TC*)set.lev;
+  P.lev_arr = R.lev_arr;
+  P.lev_sub = R.lev_sub;
+  P.lev_h0 = R.lev_h0;
+  P.lev_hd0 = R.lev_hd0;
+  P.lev_flip = P.base ^ R.base;
   return NDIAG_OK;
 }
 
@@ -431,7 +699,8 @@ GP<T, TC> params(Handle* h, int mode, int64_t t, const ScaledSet& set, const voi
   P.xnew = (T*)xnew;
   P.st = h->status;
   const int w = P.sp[0].len(0), hh = P.sp[1].len(0), d = P.sp[2].len(0);
-  smem = P.coupled ? sizeof(T) * (size_t)twin_store_size(w, hh, d) : 0;
+  P.twin_slots = P.coupled ? twin_store_size(w, hh, d) : 0;
+  smem = sizeof(T) * (size_t)P.twin_slots;
   nsub = (unsigned)(P.sp[0].p * P.sp[1].p * P.sp[2].p);
   return P;
 }
@@ -456,10 +725,17 @@ ndiag_status sweep3d_t(Handle* h, int kind, int mode, int64_t t, const double* o
   const double cellbytes = kind == KIND_SOR ? 9.0 * sizeof(TC) + 3.0 * sizeof(T)
                                             : (kind == KIND_TRI_SCALED ? 4.0 : 3.0) * sizeof(TC) + 2.0 * sizeof(T);
   const double bytes = cellbytes * (double)h->N;
+  // the pencil walk: triangular kinds, rows of the largest subdomain within KR per thread
+  const bool pencil = kind != KIND_SOR && pencil_rows(P) <= KR * GT;
+  if (pencil) ND_TRY(attach_levels(h, const_cast<ScaledSet&>(set), P, mode));  // lev is a cache of set
+  // one sweep's bytes go with its last (forward) or first (transposed) launch
+  double b_now = bytes;
   auto go = [&](auto kt, auto o1) -> ndiag_status {
     constexpr int K = decltype(kt)::value;
     constexpr bool O = decltype(o1)::value;
-    return run3d<T, TC, K, O>(h, P, nsub, smem, bytes);
+    const bool pen = pencil && P.region == REG_INTERIOR;
+    const ndiag_status st = run3d<T, TC, K, O>(h, P, nsub, smem, b_now, pen);
+    return st;
   };
   using S0 = std::integral_constant<int, KIND_SOR>;
   using S1 = std::integral_constant<int, KIND_TRI_SCALED>;
@@ -469,8 +745,22 @@ ndiag_status sweep3d_t(Handle* h, int kind, int mode, int64_t t, const double* o
   if (!transposed) {
     P.region = REG_ALL;
     if (kind == KIND_SOR) return om1 ? go(S0(), BT()) : go(S0(), BF());
-    if (kind == KIND_TRI_SCALED) return om1 ? go(S1(), BT()) : go(S1(), BF());
-    return om1 ? go(S2(), BT()) : go(S2(), BF());
+    auto fwd = [&](auto kt) -> ndiag_status {
+      if (!pencil) {
+        P.region = REG_ALL;
+        return om1 ? go(kt, BT()) : go(kt, BF());
+      }
+      if (P.coupled) {  // the coupled blocks first, then the one-cell blocks
+        P.region = REG_BLOCKS;
+        b_now = 0.0;
+        ND_TRY(om1 ? go(kt, BT()) : go(kt, BF()));
+      }
+      P.region = REG_INTERIOR;
+      b_now = bytes;
+      return om1 ? go(kt, BT()) : go(kt, BF());
+    };
+    if (kind == KIND_TRI_SCALED) return fwd(S1());
+    return fwd(S2());
   }
   // (D + w L^T) y = v: interiors, then faces, edges, corners (earlier passes
   // read from global memory); only the interior pass counts the bytes
@@ -478,6 +768,7 @@ ndiag_status sweep3d_t(Handle* h, int kind, int mode, int64_t t, const double* o
   const int last = P.coupled ? (h->dim == 3 ? REG_CORNERS : REG_EDGES) : REG_INTERIOR;
   for (int r = REG_INTERIOR; r <= last; ++r) {
     P.region = r;
+    b_now = r == REG_INTERIOR ? bytes : 0.0;
     ND_TRY(om1 ? go(S2(), BT()) : go(S2(), BF()));
   }
   return NDIAG_OK;

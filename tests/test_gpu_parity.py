@@ -1,6 +1,6 @@
 """GPU parity of the CUDA path against the CPU oracle, through the C ABI.
 
-Tolerances (derivations in the design doc):
+Tolerances:
   fp64 sweeps / applies: max |x - x_oracle| <= 1e-12 max |x_oracle|
   fp32 sweeps:           <= 2e-5  (unit roundoff 6e-8, ~30x growth along the wavefront)
   fp32 + fp16 diagonals: <= 2e-3  (coefficients rounded to 2^-11)
@@ -294,9 +294,11 @@ def test_full_size_solve_meets_tolerance_and_oracle_count(nd, big):
     x = _t(np.zeros(2048 * 2048))
     info = h.solve(nd.BICGSTAB, nd.PREC_ILU0, _t(p["b"]), x, rtol=1e-8, maxit=20000)
     assert info["relres"] <= 1e-8
-    path = os.path.join(GOLDEN, "varcoef2048.json")
-    if os.path.exists(path):
-        # BiCGSTAB's count moves under rounding (see the module docstring);
-        # at full size the oracle envelope is too costly, so 10 % is allowed.
-        gold = json.load(open(path))["decomposed"]
-        assert abs(info["iters"] - gold["iters"]) <= max(1, 0.1 * gold["iters"]), (info, gold)
+    # BiCGSTAB's count moves under rounding (see the module docstring): the
+    # oracle's own counts for this workload, unperturbed and under seven 1e-15
+    # relative perturbations of b, span the envelope (stored by
+    # tests/golden/make_golden.py), widened by 1.
+    gold = json.load(open(os.path.join(GOLDEN, "varcoef2048.json")))["decomposed"]
+    env = json.load(open(os.path.join(GOLDEN, "varcoef2048_envelope.json")))
+    lo, hi = min(env["min"], gold["iters"]) - 1, max(env["max"], gold["iters"]) + 1
+    assert lo <= info["iters"] <= hi, (info, lo, hi)

@@ -1,6 +1,6 @@
 """Pin the oracle's natural and decomposed 1D sweeps to Table 1 of the paper.
 
-Reading (stated in DESIGN.md): "N grids" = N points including both boundary
+Reading of the paper used here: "N grids" = N points including both boundary
 points, L1 error = mean over all N points, one sweep = one iteration, SGS
 alternates LR/RL every iteration, PGS(p) runs the decomposed sweep on p
 subdomains with the first subdomain sweeping left-to-right at the first
