@@ -165,6 +165,17 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
     if (S.c[axes[r]] == 0) mo |= 1 << r;
   T M[n][n], hv[n];
   int64_t gidx[n];
+  // coupling of member m to its block partner across each coupled axis
+  // (member index m ^ 2^r: constant indices, so M stays in registers)
+  auto partners = [&](int m, const int* cm, int64_t gi, T om) {
+#pragma unroll
+    for (int r = 0; r < NC; ++r) {
+      const int a = axes[r];
+      T g = ldco<T, TC>(P.c[ent(a, cm[a] ? 1 : 0)] + gi);
+      if (!OM1) g *= om;
+      M[m][m ^ (1 << r)] = g;
+    }
+  };
 #pragma unroll
   for (int m = 0; m < n; ++m) {
     int lc[3] = {own[0], own[1], own[2]}, sub = 0;
@@ -208,14 +219,11 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
         acc = __ldg(P.rhs + gi);
       }
       // upstream neighbours: block partners, or earlier blocks' members
+      partners(m, cm, gi, om);
       for (int a = 0; a < P.dim; ++a) {
         const int up = cm[a] ? 1 : 0;  // upstream side of the member along a
         if (C >> a & 1) {
-          int r = 0;
-          while (axes[r] != a) ++r;
-          T g = ldco<T, TC>(P.c[ent(a, up)] + gi);
-          if (!OM1) g *= om;
-          M[m][m ^ (1 << r)] = g;
+          // the block partner along a (set by partners)
         } else if (lc[a] >= 1) {
           T g = ldco<T, TC>(P.c[ent(a, up)] + gi);
           if (!OM1) g *= om;
@@ -235,15 +243,9 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
       // transposed: dependents are the downstream neighbours inside the
       // member's own subdomain, and the block partners
       acc = __ldg(P.rhs + gi);
+      partners(m, cm, gi, om);
       for (int a = 0; a < P.dim; ++a) {
         const int up = cm[a] ? 1 : 0, dn = 1 - up;
-        if (C >> a & 1) {
-          int r = 0;
-          while (axes[r] != a) ++r;
-          T g = ldco<T, TC>(P.c[ent(a, up)] + gi);
-          if (!OM1) g *= om;
-          M[m][m ^ (1 << r)] = g;
-        }
         // downstream neighbour inside the member's subdomain: local
         // coordinate +1 (own side), or -2 (twin side along a)
         const bool twin_axis = (sub >> a) & 1;
@@ -317,8 +319,16 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
   return xs[mo];
 }
 
+// the 8x8 corner block (one per subdomain) out of line, so that its registers
+// do not weigh on the face and edge blocks
 template <class T, class TC, int KIND, bool OM1>
-__global__ void __launch_bounds__(GT) sweep3d_kernel(GP<T, TC> P) {
+__device__ __noinline__ void corner_block(const GP<T, TC>& P, const Sub& S, const TwinIdx& TI, T* tw, int x, int y,
+                                          int z, int C, int tcode) {
+  block_solve<T, TC, KIND, OM1, 3>(P, S, TI, tw, x, y, z, C, tcode);
+}
+
+template <class T, class TC, int KIND, bool OM1>
+__global__ void __launch_bounds__(GT, sizeof(T) == 8 ? 2 : 4) sweep3d_kernel(GP<T, TC> P) {
   extern __shared__ __align__(16) unsigned char gsm[];
   T* tw = reinterpret_cast<T*>(gsm);
   const Sub S = subdomain(P, blockIdx.x);
@@ -410,7 +420,7 @@ __global__ void __launch_bounds__(GT) sweep3d_kernel(GP<T, TC> P) {
       }
       if (__popc(C) == 1) block_solve<T, TC, KIND, OM1, 1>(P, S, TI, tw, x, y, z, C, tcode);
       else if (__popc(C) == 2) block_solve<T, TC, KIND, OM1, 2>(P, S, TI, tw, x, y, z, C, tcode);
-      else block_solve<T, TC, KIND, OM1, 3>(P, S, TI, tw, x, y, z, C, tcode);
+      else corner_block<T, TC, KIND, OM1>(P, S, TI, tw, x, y, z, C, tcode);
     }
     __syncthreads();
   }
