@@ -77,6 +77,134 @@ __device__ __forceinline__ int slot9(int sub, const int* lc, int w, int h) {
   return sub == 1 ? lc[1] : (sub == 2 ? h + lc[0] : h + w);
 }
 
+// The block of own cell (x, y), which lies on the NC coupled start lines C:
+// assembled member by member in canonical order, solved, the own member
+// stored to xnew and the twins to the twin-line store.
+template <class T, class TC, int KIND, bool OM1, int NC>
+__device__ __forceinline__ void cell9(const P9<T, TC>& P, const Sub9& S, T* tw, int w, int h, int x, int y, int C) {
+  const int own[2] = {x, y};
+  int axes[2], nC = 0;
+  for (int a = 0; a < 2; ++a)
+    if (C >> a & 1) axes[nC++] = a;
+  constexpr int n = 1 << NC;  // nC == NC
+  int mo = 0;
+  for (int r = 0; r < nC; ++r)
+    if (S.c[axes[r]] == 0) mo |= 1 << r;
+  T M[n][n], hv[n];
+  int64_t gidx[n];
+#pragma unroll
+  for (int m = 0; m < n; ++m) {
+    int lc[2] = {own[0], own[1]}, sub = 0;
+    for (int r = 0; r < nC; ++r)
+      if (((m ^ mo) >> r) & 1) {
+        lc[axes[r]] = -1;
+        sub |= 1 << axes[r];
+      }
+    const int cm0 = S.c[0] ^ (sub & 1), cm1 = S.c[1] ^ ((sub >> 1) & 1);
+    // extent of the member's subdomain and its local coordinates there
+    int mlen[2], ml[2];
+    for (int a = 0; a < 2; ++a) {
+      if ((sub >> a) & 1) {
+        const int ia = a == 0 ? (S.c[0] ? S.ix + 1 : S.ix - 1) : (S.c[1] ? S.iy + 1 : S.iy - 1);
+        mlen[a] = a == 0 ? P.sx.len(ia) : P.sy.len(ia);
+        ml[a] = 0;
+      } else {
+        mlen[a] = S.len[a];
+        ml[a] = lc[a];
+      }
+    }
+    const int gx = S.gco(0, lc[0]), gy = S.gco(1, lc[1]);
+    const int64_t gi = (int64_t)gy * P.nx + gx;
+    gidx[m] = gi;
+    const T om = OM1 ? T(1) : P.om[cm0 | (cm1 << 1)];
+#pragma unroll
+    for (int k = 0; k < n; ++k) M[m][k] = T(0);
+    M[m][m] = T(1);
+    // explicit part (old values; SOR only) and the implicit part, each in
+    // the member's own neighbour order, so every CTA forms the same terms
+    T base = (KIND == KIND_TRI_UNIT) ? __ldg(P.rhs + gi) : ldco<T, TC>(P.inv + gi) * __ldg(P.rhs + gi);
+    T impl = T(0);
+    const int offs[8][2] = {{-1, 0}, {-1, -1}, {0, -1}, {1, -1}, {1, 0}, {1, 1}, {0, 1}, {-1, 1}};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int dx = offs[q][0], dy = offs[q][1];
+      const int qx = ml[0] + dx, qy = ml[1] + dy;
+      const int e = ent9(dx, dy, cm0, cm1);
+      const int ggx = gx + (cm0 ? -dx : dx), ggy = gy + (cm1 ? -dy : dy);
+      if (ggx < 0 || ggx >= P.nx || ggy < 0 || ggy >= P.ny) continue;
+      const bool upstream = q < 4;  // W, SW, S, SE
+      const bool inside = qx >= 0 && qx < mlen[0] && qy >= 0 && qy < mlen[1];
+      const int64_t gq = (int64_t)ggy * P.nx + ggx;
+      if (upstream && inside) {
+        // new value of a cell of the member's own subdomain
+        T g = ldco<T, TC>(P.c[e] + gi);
+        if (!OM1) g *= om;
+        T v;
+        if (sub == 0) {
+          v = __ldcg(P.xnew + gq);
+        } else {
+          // in S-coordinates: still on the twin line -> shared store, deeper -> global
+          const int nl[2] = {lc[0] + (cm0 == S.c[0] ? dx : -dx), lc[1] + (cm1 == S.c[1] ? dy : -dy)};
+          const bool on_line = ((sub & 1) ? nl[0] == -1 : nl[0] >= 0) && ((sub & 2) ? nl[1] == -1 : nl[1] >= 0);
+          v = on_line ? tw[slot9(sub, nl, w, h)] : __ldcg(P.xnew + gq);
+        }
+        impl = fma(g, v, impl);
+      } else if (upstream && (dx == 0 || dy == 0) && ((C >> (dx != 0 ? 0 : 1)) & 1)) {
+        // face neighbour across a coupled start line: the block partner
+        // partner index bit: the coupled axes in order (x before y)
+        const int r = NC == 2 ? (dx != 0 ? 0 : 1) : 0;
+        T g = ldco<T, TC>(P.c[e] + gi);
+        if (!OM1) g *= om;
+        M[m][m ^ (1 << r)] = g;
+      } else if (KIND == KIND_SOR) {
+        // downstream neighbours, uncoupled or diagonal ones across an interface: old values
+        base = fma(-ldco<T, TC>(P.c[e] + gi), __ldg(P.xold + gq), base);
+      }
+    }
+    T acc;
+    if (KIND == KIND_SOR) acc = OM1 ? base : fma(om, base, (T(1) - om) * __ldg(P.xold + gi));
+    else if (KIND == KIND_TRI_SCALED) acc = OM1 ? base : P.bscale * base;
+    else acc = base;
+    acc -= impl;
+    hv[m] = acc;
+  }
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    const T piv = M[k][k];
+#pragma unroll
+    for (int i = k + 1; i < n; ++i) {
+      const T f = M[i][k] / piv;
+      if (f != T(0)) {
+#pragma unroll
+        for (int j = k + 1; j < n; ++j) M[i][j] = fma(-f, M[k][j], M[i][j]);
+        hv[i] = fma(-f, hv[k], hv[i]);
+      }
+    }
+  }
+  T xs[n];
+#pragma unroll
+  for (int k = n - 1; k >= 0; --k) {
+    T s = hv[k];
+#pragma unroll
+    for (int j = k + 1; j < n; ++j) s = fma(-M[k][j], xs[j], s);
+    xs[k] = s / M[k][k];
+  }
+#pragma unroll
+  for (int m = 0; m < n; ++m) {
+    if (m == mo) {
+      P.xnew[gidx[m]] = xs[m];
+    } else {
+      int lc[2] = {own[0], own[1]}, sub = 0;
+      for (int r = 0; r < nC; ++r)
+        if (((m ^ mo) >> r) & 1) {
+          lc[axes[r]] = -1;
+          sub |= 1 << axes[r];
+        }
+      tw[slot9(sub, lc, w, h)] = xs[m];
+    }
+  }
+}
+
 template <class T, class TC, int KIND, bool OM1>
 __global__ void __launch_bounds__(T9) sweep9_kernel(P9<T, TC> P) {
   extern __shared__ __align__(16) unsigned char gsm[];
@@ -101,121 +229,10 @@ __global__ void __launch_bounds__(T9) sweep9_kernel(P9<T, TC> P) {
     for (int y = threadIdx.x; y < h; y += T9) {
       const int x = L - 2 * y;
       if (x < 0 || x >= w) continue;
-      const int own[2] = {x, y};
       const int C = ((x == 0) | ((y == 0) << 1)) & tcode;
-      int axes[2], nC = 0;
-      for (int a = 0; a < 2; ++a)
-        if (C >> a & 1) axes[nC++] = a;
-      const int n = 1 << nC;
-      int mo = 0;
-      for (int r = 0; r < nC; ++r)
-        if (S.c[axes[r]] == 0) mo |= 1 << r;
-      T M[4][4], hv[4];
-      int64_t gidx[4];
-      for (int m = 0; m < n; ++m) {
-        int lc[2] = {own[0], own[1]}, sub = 0;
-        for (int r = 0; r < nC; ++r)
-          if (((m ^ mo) >> r) & 1) {
-            lc[axes[r]] = -1;
-            sub |= 1 << axes[r];
-          }
-        const int cm0 = S.c[0] ^ (sub & 1), cm1 = S.c[1] ^ ((sub >> 1) & 1);
-        // extent of the member's subdomain and its local coordinates there
-        int mlen[2], ml[2];
-        for (int a = 0; a < 2; ++a) {
-          if ((sub >> a) & 1) {
-            const int ia = a == 0 ? (S.c[0] ? S.ix + 1 : S.ix - 1) : (S.c[1] ? S.iy + 1 : S.iy - 1);
-            mlen[a] = a == 0 ? P.sx.len(ia) : P.sy.len(ia);
-            ml[a] = 0;
-          } else {
-            mlen[a] = S.len[a];
-            ml[a] = lc[a];
-          }
-        }
-        const int gx = S.gco(0, lc[0]), gy = S.gco(1, lc[1]);
-        const int64_t gi = (int64_t)gy * P.nx + gx;
-        gidx[m] = gi;
-        const T om = OM1 ? T(1) : P.om[cm0 | (cm1 << 1)];
-        for (int k = 0; k < n; ++k) M[m][k] = T(0);
-        M[m][m] = T(1);
-        // explicit part (old values; SOR only) and the implicit part, each in
-        // the member's own neighbour order, so every CTA forms the same terms
-        T base = (KIND == KIND_TRI_UNIT) ? __ldg(P.rhs + gi) : ldco<T, TC>(P.inv + gi) * __ldg(P.rhs + gi);
-        T impl = T(0);
-        const int offs[8][2] = {{-1, 0}, {-1, -1}, {0, -1}, {1, -1}, {1, 0}, {1, 1}, {0, 1}, {-1, 1}};
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int dx = offs[q][0], dy = offs[q][1];
-          const int qx = ml[0] + dx, qy = ml[1] + dy;
-          const int e = ent9(dx, dy, cm0, cm1);
-          const int ggx = gx + (cm0 ? -dx : dx), ggy = gy + (cm1 ? -dy : dy);
-          if (ggx < 0 || ggx >= P.nx || ggy < 0 || ggy >= P.ny) continue;
-          const bool upstream = q < 4;  // W, SW, S, SE
-          const bool inside = qx >= 0 && qx < mlen[0] && qy >= 0 && qy < mlen[1];
-          const int64_t gq = (int64_t)ggy * P.nx + ggx;
-          if (upstream && inside) {
-            // new value of a cell of the member's own subdomain
-            T g = ldco<T, TC>(P.c[e] + gi);
-            if (!OM1) g *= om;
-            T v;
-            if (sub == 0) {
-              v = __ldcg(P.xnew + gq);
-            } else {
-              // in S-coordinates: still on the twin line -> shared store, deeper -> global
-              const int nl[2] = {lc[0] + (cm0 == S.c[0] ? dx : -dx), lc[1] + (cm1 == S.c[1] ? dy : -dy)};
-              const bool on_line = ((sub & 1) ? nl[0] == -1 : nl[0] >= 0) && ((sub & 2) ? nl[1] == -1 : nl[1] >= 0);
-              v = on_line ? tw[slot9(sub, nl, w, h)] : __ldcg(P.xnew + gq);
-            }
-            impl = fma(g, v, impl);
-          } else if (upstream && (dx == 0 || dy == 0) && ((C >> (dx != 0 ? 0 : 1)) & 1)) {
-            // face neighbour across a coupled start line: the block partner
-            const int a = dx != 0 ? 0 : 1;
-            int r = 0;
-            while (axes[r] != a) ++r;
-            T g = ldco<T, TC>(P.c[e] + gi);
-            if (!OM1) g *= om;
-            M[m][m ^ (1 << r)] = g;
-          } else if (KIND == KIND_SOR) {
-            // downstream neighbours, uncoupled or diagonal ones across an interface: old values
-            base = fma(-ldco<T, TC>(P.c[e] + gi), __ldg(P.xold + gq), base);
-          }
-        }
-        T acc;
-        if (KIND == KIND_SOR) acc = OM1 ? base : fma(om, base, (T(1) - om) * __ldg(P.xold + gi));
-        else if (KIND == KIND_TRI_SCALED) acc = OM1 ? base : P.bscale * base;
-        else acc = base;
-        acc -= impl;
-        hv[m] = acc;
-      }
-      for (int k = 0; k < n; ++k) {
-        const T piv = M[k][k];
-        for (int i = k + 1; i < n; ++i) {
-          const T f = M[i][k] / piv;
-          if (f != T(0)) {
-            for (int j = k + 1; j < n; ++j) M[i][j] = fma(-f, M[k][j], M[i][j]);
-            hv[i] = fma(-f, hv[k], hv[i]);
-          }
-        }
-      }
-      T xs[4];
-      for (int k = n - 1; k >= 0; --k) {
-        T s = hv[k];
-        for (int j = k + 1; j < n; ++j) s = fma(-M[k][j], xs[j], s);
-        xs[k] = s / M[k][k];
-      }
-      for (int m = 0; m < n; ++m) {
-        if (m == mo) {
-          P.xnew[gidx[m]] = xs[m];
-        } else {
-          int lc[2] = {own[0], own[1]}, sub = 0;
-          for (int r = 0; r < nC; ++r)
-            if (((m ^ mo) >> r) & 1) {
-              lc[axes[r]] = -1;
-              sub |= 1 << axes[r];
-            }
-          tw[slot9(sub, lc, w, h)] = xs[m];
-        }
-      }
+      if (C == 0) cell9<T, TC, KIND, OM1, 0>(P, S, tw, w, h, x, y, C);
+      else if (C == 3) cell9<T, TC, KIND, OM1, 2>(P, S, tw, w, h, x, y, C);
+      else cell9<T, TC, KIND, OM1, 1>(P, S, tw, w, h, x, y, C);
     }
     __syncthreads();
     if (threadIdx.x == 0 && P.coupled) {
