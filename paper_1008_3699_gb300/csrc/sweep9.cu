@@ -81,7 +81,7 @@ __device__ __forceinline__ int slot9(int sub, const int* lc, int w, int h) {
 // assembled member by member in canonical order, solved, the own member
 // stored to xnew and the twins to the twin-line store.
 template <class T, class TC, int KIND, bool OM1, int NC>
-__device__ __forceinline__ void cell9(const P9<T, TC>& P, const Sub9& S, T* tw, int w, int h, int x, int y, int C) {
+__device__ __forceinline__ T cell9(const P9<T, TC>& P, const Sub9& S, T* tw, int w, int h, int x, int y, int C) {
   const int own[2] = {x, y};
   int axes[2], nC = 0;
   for (int a = 0; a < 2; ++a)
@@ -203,6 +203,7 @@ __device__ __forceinline__ void cell9(const P9<T, TC>& P, const Sub9& S, T* tw, 
       tw[slot9(sub, lc, w, h)] = xs[m];
     }
   }
+  return xs[mo];
 }
 
 template <class T, class TC, int KIND, bool OM1>
@@ -214,6 +215,33 @@ __global__ void __launch_bounds__(T9) sweep9_kernel(P9<T, TC> P) {
   const int w = S.len[0], h = S.len[1];
   const int lmax = (w - 1) + 2 * (h - 1);
   const int tcode = S.t[0] | (S.t[1] << 1);
+  // Pencil path (triangular kinds, h <= T9): thread y meets its row's next
+  // cell x = L - 2y on every level. W is the row's previous cell (register);
+  // SE, S, SW are row y - 1's cells of levels L - 1, L - 2, L - 3, kept in a
+  // shared ring of four levels; the operands of the next level's one-cell
+  // blocks are loaded before this level's arithmetic.
+  const bool pen = KIND != KIND_SOR && h <= T9;
+  T* ring = tw + (w + h + 1);  // [4][h]
+  const int c0 = S.c[0], c1 = S.c[1];
+  const int eW = ent9(-1, 0, c0, c1), eSW = ent9(-1, -1, c0, c1), eS = ent9(0, -1, c0, c1),
+            eSE = ent9(1, -1, c0, c1);
+  const T om = OM1 ? T(1) : P.om[c0 | (c1 << 1)];
+  const int y = threadIdx.x;
+  T ni = T(0), nr = T(0), ng[4] = {T(0), T(0), T(0), T(0)};  // next level's operands
+  auto fetch = [&](int L2) {
+    const int x2 = L2 - 2 * y;
+    if (!pen || y >= h || x2 < 0 || x2 >= w) return;
+    if ((((x2 == 0) | ((y == 0) << 1)) & tcode) != 0) return;
+    const int64_t gi = (int64_t)S.gco(1, y) * P.nx + S.gco(0, x2);
+    if (KIND == KIND_TRI_SCALED) ni = ldco<T, TC>(P.inv + gi);
+    nr = __ldg(P.rhs + gi);
+    ng[0] = x2 >= 1 ? ldco<T, TC>(P.c[eW] + gi) : T(0);
+    ng[1] = (x2 >= 1 && y >= 1) ? ldco<T, TC>(P.c[eSW] + gi) : T(0);
+    ng[2] = y >= 1 ? ldco<T, TC>(P.c[eS] + gi) : T(0);
+    ng[3] = (x2 + 1 < w && y >= 1) ? ldco<T, TC>(P.c[eSE] + gi) : T(0);
+  };
+  T xr = T(0);
+  fetch(0);
   // x-neighbour across the coupled start line (its interior feeds the x-twins)
   const int nbx = S.c[0] ? ix + 1 : ix - 1;
   const unsigned* nprog = S.t[0] ? P.prog + (iy * P.sx.p + nbx) : nullptr;
@@ -226,13 +254,48 @@ __global__ void __launch_bounds__(T9) sweep9_kernel(P9<T, TC> P) {
       __syncthreads();
       if (!s_ok) return;
     }
-    for (int y = threadIdx.x; y < h; y += T9) {
+    if (pen) {
+      const T ci = ni, cr = nr, cg0 = ng[0], cg1 = ng[1], cg2 = ng[2], cg3 = ng[3];
+      if (L < lmax) fetch(L + 1);
       const int x = L - 2 * y;
-      if (x < 0 || x >= w) continue;
-      const int C = ((x == 0) | ((y == 0) << 1)) & tcode;
-      if (C == 0) cell9<T, TC, KIND, OM1, 0>(P, S, tw, w, h, x, y, C);
-      else if (C == 3) cell9<T, TC, KIND, OM1, 2>(P, S, tw, w, h, x, y, C);
-      else cell9<T, TC, KIND, OM1, 1>(P, S, tw, w, h, x, y, C);
+      if (y < h && x >= 0 && x < w) {
+        const int C = ((x == 0) | ((y == 0) << 1)) & tcode;
+        T v;
+        if (C == 0) {
+          // the one-cell block, term for term as cell9: W, SW, S, SE
+          T g[4] = {cg0, cg1, cg2, cg3};
+          if (!OM1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) g[q] *= om;
+          }
+          const T* rp = ring + (y - 1);
+          T impl = T(0);
+          if (x >= 1) impl = fma(g[0], xr, impl);
+          if (x >= 1 && y >= 1) impl = fma(g[1], rp[((L - 3) & 3) * h], impl);
+          if (y >= 1) impl = fma(g[2], rp[((L - 2) & 3) * h], impl);
+          if (x + 1 < w && y >= 1) impl = fma(g[3], rp[((L - 1) & 3) * h], impl);
+          T base = KIND == KIND_TRI_UNIT ? cr : ci * cr;
+          T acc = (KIND == KIND_TRI_SCALED && !OM1) ? P.bscale * base : base;
+          acc -= impl;
+          P.xnew[(int64_t)S.gco(1, y) * P.nx + S.gco(0, x)] = acc;
+          v = acc;
+        } else if (C == 3) {
+          v = cell9<T, TC, KIND, OM1, 2>(P, S, tw, w, h, x, y, C);
+        } else {
+          v = cell9<T, TC, KIND, OM1, 1>(P, S, tw, w, h, x, y, C);
+        }
+        ring[(L & 3) * h + y] = v;
+        xr = v;
+      }
+    } else {
+      for (int y2 = threadIdx.x; y2 < h; y2 += T9) {
+        const int x = L - 2 * y2;
+        if (x < 0 || x >= w) continue;
+        const int C = ((x == 0) | ((y2 == 0) << 1)) & tcode;
+        if (C == 0) cell9<T, TC, KIND, OM1, 0>(P, S, tw, w, h, x, y2, C);
+        else if (C == 3) cell9<T, TC, KIND, OM1, 2>(P, S, tw, w, h, x, y2, C);
+        else cell9<T, TC, KIND, OM1, 1>(P, S, tw, w, h, x, y2, C);
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0 && P.coupled) {
@@ -299,7 +362,8 @@ P9<T, TC> params9(Handle* h, int mode, int64_t t, const ScaledSet& set, const vo
 template <class T, class TC, int KIND, bool OM1>
 ndiag_status run9(Handle* h, P9<T, TC>& P, unsigned nsub, double bytes) {
   const int w = P.sx.len(0), hh = P.sy.len(0);
-  const size_t smem = sizeof(T) * (size_t)(w + hh + 1);
+  // twin lines, then the pencil path's four-level ring
+  const size_t smem = sizeof(T) * (size_t)(w + hh + 1 + 4 * hh);
   static bool attr = false;
   if (!attr) {
     ND_CUDA(cudaFuncSetAttribute(sweep9_kernel<T, TC, KIND, OM1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
