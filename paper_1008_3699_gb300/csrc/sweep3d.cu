@@ -41,7 +41,7 @@ constexpr int GT = 256;  // threads per CTA
 enum { REG_ALL = 0, REG_INTERIOR = 1, REG_FACES = 2, REG_EDGES = 3, REG_CORNERS = 4, REG_BLOCKS = 5 };
 
 template <class T, class TC>
-struct GP {
+struct GP {  // 3D only (dim == 3)
   int n[3];
   int64_t stride[3];  // 1, nx, nx * ny
   Split sp[3];
@@ -201,7 +201,8 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
     if (!P.transposed) {
       if (KIND == KIND_SOR) {
         T e = ldco<T, TC>(P.inv + gi) * __ldg(P.rhs + gi);
-        for (int a = 0; a < P.dim; ++a) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
           const int dn = cm[a] ? 0 : 1;  // downstream side of the member along a
           const int gd = gc[a] + (dn ? 1 : -1);
           if (gd >= 0 && gd < P.n[a])
@@ -220,7 +221,8 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
       }
       // upstream neighbours: block partners, or earlier blocks' members
       partners(m, cm, gi, om);
-      for (int a = 0; a < P.dim; ++a) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
         const int up = cm[a] ? 1 : 0;  // upstream side of the member along a
         if (C >> a & 1) {
           // the block partner along a (set by partners)
@@ -244,7 +246,8 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
       // member's own subdomain, and the block partners
       acc = __ldg(P.rhs + gi);
       partners(m, cm, gi, om);
-      for (int a = 0; a < P.dim; ++a) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
         const int up = cm[a] ? 1 : 0, dn = 1 - up;
         // downstream neighbour inside the member's subdomain: local
         // coordinate +1 (own side), or -2 (twin side along a)
@@ -382,7 +385,8 @@ __global__ void __launch_bounds__(GT, sizeof(T) == 8 ? 2 : 4) sweep3d_kernel(GP<
         if (!P.transposed) {
           if (KIND == KIND_SOR) {
             T e = ldco<T, TC>(P.inv + gi) * __ldg(P.rhs + gi);
-            for (int a = 0; a < P.dim; ++a) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
               const int dn = S.c[a] ? 0 : 1;
               const int gd = gc[a] + (dn ? 1 : -1);
               if (gd >= 0 && gd < P.n[a])
@@ -398,7 +402,8 @@ __global__ void __launch_bounds__(GT, sizeof(T) == 8 ? 2 : 4) sweep3d_kernel(GP<
           } else {
             acc = __ldg(P.rhs + gi);
           }
-          for (int a = 0; a < P.dim; ++a) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
             if (own[a] < 1) continue;
             const int up = S.c[a] ? 1 : 0;
             T g = ldco<T, TC>(P.c[ent(a, up)] + gi);
@@ -407,7 +412,8 @@ __global__ void __launch_bounds__(GT, sizeof(T) == 8 ? 2 : 4) sweep3d_kernel(GP<
           }
         } else {
           acc = __ldg(P.rhs + gi);
-          for (int a = 0; a < P.dim; ++a) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
             if (own[a] + 1 >= S.len[a]) continue;
             const int dn = S.c[a] ? 0 : 1;
             T g = ldco<T, TC>(P.c[ent(a, dn)] + gi);
@@ -583,7 +589,8 @@ __global__ void __launch_bounds__(GT) factor3d_kernel(GP<T, TC> P, const double*
       int64_t gi = 0;
       for (int a = 0; a < 3; ++a) gi += (int64_t)S.gco(a, lc[a]) * P.stride[a];
       double di = A[gi];
-      for (int a = 0; a < P.dim; ++a) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
         if (lc[a] < 1) continue;
         const int up = S.c[a] ? 1 : 0;
         const int64_t gp = gi + (up ? P.stride[a] : -P.stride[a]);
