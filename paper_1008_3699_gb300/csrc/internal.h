@@ -145,6 +145,9 @@ struct Split {
   __host__ __device__ int lo(int k) const { return k * q + (k < r ? k : r); }
   __host__ __device__ int len(int k) const { return q + (k < r ? 1 : 0); }
 };
+// 9-point sweeps (sweep9.cu): whether subdomains of this height need all CTAs
+// resident (their x-interfaces advance in step through global memory)
+bool sweep9_needs_residency(int64_t ny, int py);
 // part holding coordinate x
 __host__ __device__ inline int split_find(const Split& s, int x) {
   const int big = s.r * (s.q + 1);

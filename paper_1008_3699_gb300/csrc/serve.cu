@@ -124,9 +124,10 @@ void worker(ndiag_server* S) {
       S->max_running = std::max(S->max_running, S->running);
     }
     j->t_start = Clock::now();
-    if (j->req.stencil == 9) {
-      // the 9-point sweep keeps the CTAs of an x-interface in step and needs
-      // all of them resident: one such solve at a time
+    if (j->req.stencil == 9 && nd::sweep9_needs_residency(j->req.n[1], j->req.sub[1])) {
+      // tall 9-point subdomains keep the CTAs of an x-interface in step
+      // through global memory and need all of them resident: one such solve
+      // at a time
       std::lock_guard<std::mutex> lk9(S->mu9);
       run_job(*j, s);
     } else {

@@ -39,6 +39,13 @@ struct P9 {
   T bscale;
   unsigned* prog;  // per subdomain: levels completed (zeroed before the launch)
   DevStatus* st;
+  // paired mode: the two subdomains of every coupled x-interface share one
+  // CTA (half the threads each), so their lockstep is the CTA's own barrier
+  int paired;
+  int pair_par;    // parity of the x index that starts a pair
+  int units;       // CTAs per row of subdomains
+  int lmax_all;    // levels of the largest subdomain
+  int half_elems;  // shared elements per subdomain (twin lines and ring)
 };
 
 // entry of the neighbour at local offset (dx, dy) for corner bits (cx, cy)
@@ -210,27 +217,43 @@ template <class T, class TC, int KIND, bool OM1>
 __global__ void __launch_bounds__(T9) sweep9_kernel(P9<T, TC> P) {
   extern __shared__ __align__(16) unsigned char gsm[];
   T* tw = reinterpret_cast<T*>(gsm);
-  const int ix = (int)(blockIdx.x % (unsigned)P.sx.p), iy = (int)(blockIdx.x / (unsigned)P.sx.p);
+  int ix, iy, lt = threadIdx.x, stride = T9;
+  bool active = true;
+  if (P.paired) {  // unit k of row iy: subdomains start, start + 1 (or start alone)
+    iy = (int)(blockIdx.x / (unsigned)P.units);
+    const int k = (int)(blockIdx.x % (unsigned)P.units);
+    const int start = P.pair_par == 0 ? 2 * k : (k == 0 ? 0 : 2 * k - 1);
+    const int cnt = (P.pair_par == 1 && k == 0) ? 1 : min(2, P.sx.p - start);
+    const int half = threadIdx.x >= T9 / 2 ? 1 : 0;
+    active = half < cnt;
+    ix = start + (active ? half : 0);
+    lt = threadIdx.x - half * (T9 / 2);
+    stride = T9 / 2;
+    tw += half * P.half_elems;
+  } else {
+    ix = (int)(blockIdx.x % (unsigned)P.sx.p);
+    iy = (int)(blockIdx.x / (unsigned)P.sx.p);
+  }
   const Sub9 S = sub9(P, ix, iy);
   const int w = S.len[0], h = S.len[1];
-  const int lmax = (w - 1) + 2 * (h - 1);
+  const int lmax = P.paired ? P.lmax_all : (w - 1) + 2 * (h - 1);
   const int tcode = S.t[0] | (S.t[1] << 1);
   // Pencil path (triangular kinds, h <= T9): thread y meets its row's next
   // cell x = L - 2y on every level. W is the row's previous cell (register);
   // SE, S, SW are row y - 1's cells of levels L - 1, L - 2, L - 3, kept in a
   // shared ring of four levels; the operands of the next level's one-cell
   // blocks are loaded before this level's arithmetic.
-  const bool pen = KIND != KIND_SOR && h <= T9;
+  const bool pen = KIND != KIND_SOR && h <= stride;
   T* ring = tw + (w + h + 1);  // [4][h]
   const int c0 = S.c[0], c1 = S.c[1];
   const int eW = ent9(-1, 0, c0, c1), eSW = ent9(-1, -1, c0, c1), eS = ent9(0, -1, c0, c1),
             eSE = ent9(1, -1, c0, c1);
   const T om = OM1 ? T(1) : P.om[c0 | (c1 << 1)];
-  const int y = threadIdx.x;
+  const int y = lt;
   T ni = T(0), nr = T(0), ng[4] = {T(0), T(0), T(0), T(0)};  // next level's operands
   auto fetch = [&](int L2) {
     const int x2 = L2 - 2 * y;
-    if (!pen || y >= h || x2 < 0 || x2 >= w) return;
+    if (!pen || !active || y >= h || x2 < 0 || x2 >= w) return;
     if ((((x2 == 0) | ((y == 0) << 1)) & tcode) != 0) return;
     const int64_t gi = (int64_t)S.gco(1, y) * P.nx + S.gco(0, x2);
     if (KIND == KIND_TRI_SCALED) ni = ldco<T, TC>(P.inv + gi);
@@ -244,7 +267,7 @@ __global__ void __launch_bounds__(T9) sweep9_kernel(P9<T, TC> P) {
   fetch(0);
   // x-neighbour across the coupled start line (its interior feeds the x-twins)
   const int nbx = S.c[0] ? ix + 1 : ix - 1;
-  const unsigned* nprog = S.t[0] ? P.prog + (iy * P.sx.p + nbx) : nullptr;
+  const unsigned* nprog = (S.t[0] && !P.paired) ? P.prog + (iy * P.sx.p + nbx) : nullptr;
   __shared__ int s_ok;
   if (threadIdx.x == 0) s_ok = 1;
   __syncthreads();
@@ -258,7 +281,7 @@ __global__ void __launch_bounds__(T9) sweep9_kernel(P9<T, TC> P) {
       const T ci = ni, cr = nr, cg0 = ng[0], cg1 = ng[1], cg2 = ng[2], cg3 = ng[3];
       if (L < lmax) fetch(L + 1);
       const int x = L - 2 * y;
-      if (y < h && x >= 0 && x < w) {
+      if (active && y < h && x >= 0 && x < w) {
         const int C = ((x == 0) | ((y == 0) << 1)) & tcode;
         T v;
         if (C == 0) {
@@ -288,7 +311,7 @@ __global__ void __launch_bounds__(T9) sweep9_kernel(P9<T, TC> P) {
         xr = v;
       }
     } else {
-      for (int y2 = threadIdx.x; y2 < h; y2 += T9) {
+      for (int y2 = lt; active && y2 < h; y2 += stride) {
         const int x = L - 2 * y2;
         if (x < 0 || x >= w) continue;
         const int C = ((x == 0) | ((y2 == 0) << 1)) & tcode;
@@ -298,7 +321,7 @@ __global__ void __launch_bounds__(T9) sweep9_kernel(P9<T, TC> P) {
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && P.coupled) {
+    if (threadIdx.x == 0 && P.coupled && !P.paired) {
       __threadfence();
       st_release(P.prog + blockIdx.x, (unsigned)(L + 1));
     }
@@ -362,8 +385,19 @@ P9<T, TC> params9(Handle* h, int mode, int64_t t, const ScaledSet& set, const vo
 template <class T, class TC, int KIND, bool OM1>
 ndiag_status run9(Handle* h, P9<T, TC>& P, unsigned nsub, double bytes) {
   const int w = P.sx.len(0), hh = P.sy.len(0);
-  // twin lines, then the pencil path's four-level ring
-  const size_t smem = sizeof(T) * (size_t)(w + hh + 1 + 4 * hh);
+  // twin lines, then the pencil path's four-level ring (per subdomain)
+  P.half_elems = w + hh + 1 + 4 * hh;
+  // pairing: coupled x-interfaces join ix and ix + 1 where ix has the parity
+  // at which a subdomain starts at its max-x side
+  P.paired = P.coupled && hh <= T9 / 2 && P.sx.p > 1;
+  if (P.paired) {
+    P.pair_par = (P.base & 1) ? 0 : 1;
+    const int px = P.sx.p;
+    P.units = P.pair_par == 0 ? (px + 1) / 2 : 1 + px / 2;
+    P.lmax_all = (w - 1) + 2 * (hh - 1);
+    nsub = (unsigned)(P.units * P.sy.p);
+  }
+  const size_t smem = sizeof(T) * (size_t)P.half_elems * (P.paired ? 2 : 1);
   static bool attr = false;
   if (!attr) {
     ND_CUDA(cudaFuncSetAttribute(sweep9_kernel<T, TC, KIND, OM1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -371,7 +405,7 @@ ndiag_status run9(Handle* h, P9<T, TC>& P, unsigned nsub, double bytes) {
     attr = true;
   }
   if (smem > 96 * 1024) return NDIAG_EINVAL;
-  if (P.coupled) {
+  if (P.coupled && !P.paired) {
     // the x-interfaces advance in step: every CTA must be resident
     int per_sm = 0;
     ND_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep9_kernel<T, TC, KIND, OM1>, T9, smem));
@@ -397,6 +431,18 @@ ndiag_status run9(Handle* h, P9<T, TC>& P, unsigned nsub, double bytes) {
   prof_end(h, slot, bytes);
   return NDIAG_OK;
 }
+
+}  // namespace
+
+// Whether a decomposed 9-point sweep with rows of subdomains of height
+// ceil(ny / py) keeps its CTAs in step through global memory (subdomains
+// taller than a pair CTA's half), and so needs every CTA resident.
+bool sweep9_needs_residency(int64_t ny, int py) {
+  if (py < 1) return true;
+  return (ny + py - 1) / py > T9 / 2;
+}
+
+namespace {
 
 template <class T, class TC>
 ndiag_status sweep9_t(Handle* h, int kind, int mode, int64_t t, const double* omega, const ScaledSet& set,
