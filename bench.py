@@ -383,6 +383,12 @@ def workload_poisson64(args):
                                 omega=p["omega"], mode=mode)
         out[name] = {k: info[k] for k in ("iters", "relres", "wall_s")}
         h.close()
+    h = nd.NDiag(2, p["n"], 5, p["diags"], p["sub"], "fp64")
+    b = torch.tensor(p["b"], device="cuda")
+    t0 = time.perf_counter()
+    om, its = h.tune_omega(b, rtol=1e-8, maxit=20000, budget=60, omega=p["omega"])
+    out["decomposed_tuned_omega"] = {"iters": its, "omega": om, "tune_s": time.perf_counter() - t0}
+    h.close()
     print(json.dumps({"workload": "poisson2d-64x64-5pt-fp64-sor-2x2", "metric": "SOR sweeps to rel-res 1e-8",
                       "omega": p["omega"], **out}))
 

@@ -203,6 +203,28 @@ ndiag_status krylov_solve(ndiag* h, int method, int precond, int mode, const dou
                           ndiag_solve_info* info);
 
 /*
+ * ndiag_tune_omega -- a relaxation factor per sweep direction for the
+ * stationary decomposed SOR iteration. The paper relaxes the sweep directions
+ * separately (omega_L, omega_R of Tables 2-5, over- and under-relaxation, with
+ * the optimal factors searched in [0, 2]; Theorems 1 and 2 give sufficient
+ * conditions for convergence with different factors). This runs a coordinate
+ * search over the 2^dim factors (one per start corner, as krylov_solve's
+ * omega[]), each trial a full krylov_solve(NDIAG_STATIONARY, DECOMPOSED) from
+ * x = 0, minimising the number of sweeps to rtol.
+ *   b       fp64 right-hand side, DEVICE or HOST pointer.
+ *   rtol, maxit as krylov_solve; a trial that does not converge costs maxit + 1.
+ *   budget  the most trial solves to spend (>= 1).
+ *   omega   HOST array of 2^dim factors in (0, 2): the start point on entry, the
+ *           best factors found on return.
+ *   iters   out: sweeps of the returned factors.
+ * The library allocates one device vector for the trials and frees it.
+ * Errors: NDIAG_EINVAL (arguments), NDIAG_ENOMEM, NDIAG_ENOCONV (no trial
+ * converged), or a trial solve's device error.
+ */
+ndiag_status ndiag_tune_omega(ndiag* h, const double* b, double rtol, int maxit, int budget, double* omega,
+                              int* iters);
+
+/*
  * Counters of the library's own kernels on a handle, for measurement.
  *  launches        kernels the library launched since the last ndiag_profile
  *  sweep_launches  sweep kernels among them (one sweep = N cell updates; an

@@ -27,7 +27,7 @@ PREC_NONE, PREC_SSOR, PREC_ILU0 = 0, 1, 2
 # every symbol include/ndiag.h declares
 EXPORTED = ["ndiag_set_allocator", "ndiag_last_error", "ndiag_create", "ndiag_destroy", "ndiag_cells",
             "ndiag_precision", "sor_sweep", "ssor_apply", "ilu0_factor", "ilu0_apply", "ndiag_residual",
-            "krylov_solve", "ndiag_profile", "ndiag_read_counters", "ilu0_apply_noalloc",
+            "krylov_solve", "ndiag_tune_omega", "ndiag_profile", "ndiag_read_counters", "ilu0_apply_noalloc",
             "ndiag_batch_create", "ndiag_batch_autotune", "ndiag_batch_tiles", "ndiag_batch_solve",
             "ndiag_batch_cells", "ndiag_batch_launches", "ndiag_batch_destroy",
             "ndiag_server_create", "serve_submit", "serve_poll", "ndiag_server_wait", "ndiag_server_stats",
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
     L.ilu0_apply_noalloc.argtypes = [P, P, P]
     L.ndiag_residual.argtypes = [P, P, P, P, ctypes.POINTER(D)]
     L.krylov_solve.argtypes = [P, I, I, I, P, D, I, P, P, ctypes.POINTER(SolveInfo)]
+    L.ndiag_tune_omega.argtypes = [P, P, D, I, I, P, ctypes.POINTER(I)]
     L.ndiag_profile.argtypes = [P, I]
     L.ndiag_read_counters.argtypes = [P, ctypes.POINTER(Counters)]
     L.ndiag_batch_create.argtypes = [ctypes.POINTER(P), I, P, P, P, P, D, P]
@@ -245,6 +246,17 @@ class NDiag:
             _check(self.L, st)
         return dict(iters=info.iterations, outer=info.outer, relres=info.relres, seconds=info.seconds,
                     status=STATUS_NAMES[st])
+
+
+    def tune_omega(self, b, rtol=1e-8, maxit=20000, budget=60, omega=1.0):
+        """Per-direction relaxation factors for the stationary decomposed SOR
+        iteration (coordinate search on the GPU). Returns (factors, sweeps)."""
+        om = _omega(omega, self.dim).copy()
+        its = ctypes.c_int(0)
+        st = self.L.ndiag_tune_omega(self.h, _ptr(b), float(rtol), int(maxit), int(budget), _ptr(om),
+                                     ctypes.byref(its))
+        _check(self.L, st)
+        return [float(v) for v in om[: 1 << self.dim]], its.value
 
 
 class Batch:

@@ -133,6 +133,21 @@ def pin_krylov_counts(L, method):
         return False
 
 
+def pin_table5_ssour(L):
+    # Table 5: SSOUR at 41 points, omega_L = 0.24825 on the LR sweep and
+    # omega_R = 1.87087 on the RL sweep, 58 iterations
+    n = 39
+    d, b = W.laplace1d(n)
+    pb = oracle.Problem(1, (n,), 3, d, (1,), library=L)
+    x, exact, k = np.zeros(n), np.arange(1, n + 1) / 40, 0
+    while k < 3000:
+        x = pb.sor_sweep(oracle.DECOMPOSED, k, [0.24825, 1.87087], b, x)
+        k += 1
+        if np.abs(x - exact).sum() / 41 < 1e-3:
+            break
+    return k == 58
+
+
 MUTANTS = [
     ("no interface coupling",
      "  return q_up_in_i && i_up_in_q;", "  return false;",
@@ -167,6 +182,9 @@ MUTANTS = [
     ("PCG beta from the wrong inner products",
      "      const double beta = rz2 / rz;", "      const double beta = rz / rz2;",
      [lambda L: pin_krylov_counts(L, "pcg")]),
+    ("relaxation factor of the opposite direction",
+     "    const double wi = omega[pl.corner[i]];", "    const double wi = omega[pl.corner[i] ^ 1];",
+     [pin_table5_ssour]),
     ("lexicographic order reversed",
      "    if (kq != ki) return kq < ki;", "    if (kq != ki) return kq > ki;",
      [pin_table1_pgs2, pin_printed_systems]),
