@@ -187,12 +187,18 @@ struct Scal {
   int *act, *oact, *iters, *outer, *nact;
 };
 
-// inner start: rz = (r, z) (in tmp), rr0 = (r, r) (in rr); active = outer-active and rr0 > 0
-__global__ void k_inner_init(int np, Scal s) {
+// inner start: rz = (r, z) (in tmp); the inner stop threshold on (r, r):
+// t^2 (r0, r0) with t = 0.5 rtol ||b|| / ||r_outer|| clamped to [1e-6, 1e-3]
+// (one inner solve aims at the outer tolerance; fp32 gains nothing below
+// 1e-6); active = outer-active and (r0, r0) > 0
+__global__ void k_inner_init(int np, Scal s, double rtol) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
   s.rz[p] = s.tmp[p];
-  s.r0r0[p] = s.rr[p];
+  const double rn = sqrt(s.rr64[p]);
+  double t = rn > 0.0 ? 0.5 * rtol * sqrt(s.bb[p]) / rn : 1e-3;
+  t = fmin(1e-3, fmax(1e-6, t));
+  s.r0r0[p] = s.rr[p] * t * t;
   s.act[p] = s.oact[p] && s.rr[p] > 0.0;
 }
 __global__ void k_alpha(int np, Scal s) {
@@ -208,7 +214,7 @@ __global__ void k_check(int np, Scal s, double tol2) {
   if (p >= np) return;
   if (s.act[p]) {
     s.iters[p] += 1;
-    if (s.rr[p] <= tol2 * s.r0r0[p]) s.act[p] = 0;
+    if (s.rr[p] <= tol2 * s.r0r0[p]) s.act[p] = 0;  // r0r0 holds the threshold (tol2 = 1)
   }
 }
 // beta = (r, z)_new / (r, z)
@@ -372,7 +378,7 @@ ndiag_status batch_solve(ndiag_batch* B, const double* b, double* x, double rtol
                          std::vector<int>& iters, std::vector<int>& outer, std::vector<double>& relres) {
   const Blocks bl = blocks(B);
   const int g = B->nblk, np = B->np, pg = (np + 127) / 128;
-  const double tol_in = 1e-5, tol2 = tol_in * tol_in;
+  const double tol2 = 1.0;  // the per-problem inner thresholds are set by k_inner_init
   // ||b||^2 per problem
   ND_CUDA(cudaMemcpyAsync(B->b64, b, sizeof(double) * B->Ntot, cudaMemcpyDeviceToDevice, B->stream));
   ND_CUDA(cudaMemcpyAsync(B->x64, x, sizeof(double) * B->Ntot, cudaMemcpyDeviceToDevice, B->stream));
@@ -404,7 +410,7 @@ ndiag_status batch_solve(ndiag_batch* B, const double* b, double* x, double rtol
     ND_TRY(reduce(B, B->sc.tmp));
     k_dot<<<g, VT, 0, B->stream>>>(bl, B->r32, B->r32, B->part);
     ND_TRY(reduce(B, B->sc.rr));
-    k_inner_init<<<pg, 128, 0, B->stream>>>(np, B->sc);
+    k_inner_init<<<pg, 128, 0, B->stream>>>(np, B->sc, rtol);
     k_pupd<<<g, VT, 0, B->stream>>>(bl, B->sc.beta, B->z32, B->p32, 1);
     ND_CUDA(cudaGetLastError());
     // inner iterations in captured chunks

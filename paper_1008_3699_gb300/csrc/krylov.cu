@@ -2,6 +2,7 @@
 // iteration, and fp64 iterative refinement around fp32 inner solves. Scalars
 // stay on the device; the host reads the residual norms once or twice per
 // iteration to decide convergence.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 
@@ -350,7 +351,10 @@ extern "C" ndiag_status krylov_solve(ndiag* h, int method, int precond, int mode
     ND_TRY(pull(h));
     bnorm = std::sqrt(h->red_host[SC_BB]);
     const double tol = rtol * (bnorm > 0 ? bnorm : 1.0);
-    const double inner_rtol = 1e-5;
+    // inner tolerance: aim at the outer tolerance with one inner solve, but
+    // not below 1e-6 relative (where fp32 sweeps and vectors stop gaining), and
+    // never looser than 1e-3
+    const double inner_floor = 1e-6, inner_ceil = 1e-3;
     int max_outer = 60;
     for (;;) {
       // fp64 residual of the outer iterate, delivered in fp32 to the inner solve
@@ -368,7 +372,7 @@ extern "C" ndiag_status krylov_solve(ndiag* h, int method, int precond, int mode
       int it_in = 0;
       // the inner solve's right-hand side lives in V.t; copy it out first
       ND_TRY(vcopy<float>(h, V.t, (float*)r64));
-      const double tol_in = inner_rtol * rn;
+      const double tol_in = std::min(inner_ceil, std::max(inner_floor, 0.5 * tol / rn)) * rn;
       ndiag_status si;
       if (method == NDIAG_PCG) si = pcg<float>(h, P, (float*)r64, e, V, tol_in, maxit - iters, false, true, &it_in);
       else if (method == NDIAG_BICGSTAB)
