@@ -331,7 +331,7 @@ __device__ __noinline__ void corner_block(const GP<T, TC>& P, const Sub& S, cons
 }
 
 template <class T, class TC, int KIND, bool OM1>
-__global__ void __launch_bounds__(GT, sizeof(T) == 8 ? 2 : 4) sweep3d_kernel(GP<T, TC> P) {
+__global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
   extern __shared__ __align__(16) unsigned char gsm[];
   T* tw = reinterpret_cast<T*>(gsm);
   const Sub S = subdomain(P, blockIdx.x);
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(GT, sizeof(T) == 8 ? 2 : 4) sweep3d_kernel(GP<
     // of a level enumerates face a = c / umax (coordinate a = 0), the cell
     // taken on the first face where it has a zero coordinate.
     const int nq = blocks_only ? 3 * umax : h * d;
-    for (int q = threadIdx.x; q < nq; q += GT) {
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
       int x, y, z;
       if (!blocks_only) {
         y = q % h;
@@ -623,7 +623,10 @@ ndiag_status run3d(Handle* h, const GP<T, TC>& P, unsigned nsub, size_t smem, do
       return NDIAG_OK;
     }
   }
-  sweep3d_kernel<T, TC, KIND, OM1><<<nsub, GT, smem, h->stream>>>(P);
+  // the block passes have at most 3 x (largest side) cells per level: half
+  // the threads, so four CTAs fit an SM with up to 128 registers each
+  const bool blocks = P.region != REG_ALL && P.region != REG_INTERIOR;
+  sweep3d_kernel<T, TC, KIND, OM1><<<nsub, blocks ? GT / 2 : GT, smem, h->stream>>>(P);
   ND_CUDA(cudaGetLastError());
   prof_end(h, slot, bytes);
   return NDIAG_OK;
