@@ -420,6 +420,15 @@ def workload_poisson3d(args):
         b = torch.tensor(p["b"], device="cuda")
         x = torch.zeros_like(b)
         info = _timed_solve(torch, h, nd.PCG, nd.PREC_SSOR, b, x, rtol=1e-8, maxit=5000)
+        # algorithmic bytes of one SSOR apply: forward sweep (inv, 3 entries, r,
+        # tmp) and transposed solve (3 entries, tmp, z), each value once
+        wc, wv = (8, 8) if prec == "fp64" else (4, 4)
+        apply_bytes = N * ((4 * wc + 2 * wv) + (3 * wc + 2 * wv))
+        peak, kind = measured_peaks()
+        gbs = apply_bytes / (apply_ms / 1e3) / 1e9
+        out[prec + "_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                   "frac": gbs / peak, "peak_kind": kind,
+                                   "kernel": "SSOR apply (sweep3d_kernel block passes + sweep3d_pencil_kernel)"}
         out[prec] = {"ssor_apply_ms": apply_ms, "sweep_gcell_per_s": 2 * N / apply_ms / 1e6,
                      **{k: info[k] for k in ("iters", "outer", "relres", "wall_s")}}
         h.close()
@@ -497,12 +506,35 @@ def workload_serving(args):
     st = S.stats()
     S.close()
     lat = np.array([r["latency_s"] for r, _ in res])
+    # the 9-point sweep alone: ILU(0) applies of the largest request size
+    n9 = 2048
+    h9 = nd.NDiag(2, (n9, n9), 9, W.convdiff9(n9, 6.0, 1.1), (16, 16), "fp64")
+    h9.ilu0_factor(nd.DECOMPOSED)
+    r9 = torch.tensor(W.uniform_rhs(n9 * n9, 5), device="cuda")
+    z9 = torch.empty_like(r9)
+    for _ in range(2):
+        h9.ilu0_apply(r9, z9)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(5):
+        h9.ilu0_apply(r9, z9)
+    e1.record()
+    torch.cuda.synchronize()
+    h9.close()
+    ms9 = e0.elapsed_time(e1) / 5
+    bytes9 = n9 * n9 * ((5 * 8 + 2 * 8) + (4 * 8 + 2 * 8))  # forward inv, 4 entries, r, y; backward 4 entries, y, z
+    peak, kind = measured_peaks()
+    gbs9 = bytes9 / (ms9 / 1e3) / 1e9
     print(json.dumps({"workload": f"serving-{count}-requests-poisson-arrivals-2000/s",
                       "metric": "solves/s; p50/p99 latency at rel-res 1e-8",
                       "solves_per_s": count / span, "p50_latency_s": float(np.percentile(lat, 50)),
                       "p99_latency_s": float(np.percentile(lat, 99)),
                       "ok": sum(r["status"] == "OK" for r, _ in res),
-                      "relres_max": max(r["relres"] for r, _ in res), "max_running": st["max_running"]}))
+                      "relres_max": max(r["relres"] for r, _ in res), "max_running": st["max_running"],
+                      "ninept_ilu_apply_2048": {"ms": ms9, "roofline": {
+                          "bound": "hbm", "achieved": gbs9, "peak": peak, "unit": "GB/s", "frac": gbs9 / peak,
+                          "peak_kind": kind, "kernel": "sweep9_kernel (ILU(0) forward and backward, fp64)"}}}))
 
 
 EXTRA = {"poisson64": workload_poisson64, "poisson3d": workload_poisson3d,

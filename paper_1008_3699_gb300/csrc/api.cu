@@ -206,6 +206,25 @@ ndiag_status do_ilu_apply(Handle* h, const void* r, void* z) {
   return NDIAG_OK;
 }
 
+// The ILU(0) apply of a right-hand side given already scaled by the pivots,
+// rs = d~^-1 .* r (2D 5-point): the forward sweep then solves the unit form
+// (I + D~^-1 L_J) y = rs, operation for operation the same values as
+// do_ilu_apply, with the scaling done by the caller's vector kernel.
+bool ilu_prescaled_ok(const Handle* h) {
+  return h->dim == 2 && h->stencil == 5 && h->precision == NDIAG_FP64 && h->ilu_mode == NDIAG_DECOMPOSED;
+}
+const double* ilu_pivot_inverse(const Handle* h) { return (const double*)h->ilu.base; }
+ndiag_status do_ilu_apply_pre(Handle* h, const void* rs, void* z) {
+  if (!ilu_prescaled_ok(h)) {
+    set_error("pre-scaled ILU(0) apply needs a decomposed 2D 5-point fp64 factorisation");
+    return NDIAG_ESTATE;
+  }
+  ND_TRY(ensure_tmp(h));
+  const int64_t tf = fwd_phase(h->dim);
+  ND_TRY(launch_sweep2d(h, KIND_TRI_UNIT, h->ilu_mode, tf, nullptr, h->ilu, rs, nullptr, h->tmp));
+  return launch_sweep2d(h, KIND_TRI_UNIT, h->ilu_mode, tf ^ 1, nullptr, h->ilu, h->tmp, nullptr, z);
+}
+
 ndiag_status check_device_status(Handle* h) { return check_status(h); }
 
 // z = w(2-w) (D + w L_J^T)^-1 D (D + w L_J)^-1 r   (forward phase J)

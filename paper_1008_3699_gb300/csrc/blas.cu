@@ -260,9 +260,12 @@ __global__ void __launch_bounds__(BT, BPS) dots_kernel(int64_t N, const T* __res
 
 // ---- BiCGSTAB steps (scalars live in device memory) ----
 // p = r + beta (p - om v),  beta = (rho/rho_old)(alpha/om)
+// sp (optional) = inv .* p: the right-hand side of a forward sweep whose
+// diagonal scaling is taken here (the pre-scaled ILU(0) apply)
 template <class T>
 __global__ void __launch_bounds__(BT, BPS) bicg_p_kernel(int64_t N, const T* __restrict__ r, T* __restrict__ p,
-                                                         const T* __restrict__ v, const double* sc, int first) {
+                                                         const T* __restrict__ v, const double* sc, int first,
+                                                         const T* __restrict__ inv, T* __restrict__ sp) {
   const double rho = sc[SC_RHO], rho_old = sc[SC_RHO_OLD], alpha = sc[SC_ALPHA], om = sc[SC_OM];
   const double beta = first ? 0.0 : (rho / rho_old) * (alpha / om);
   constexpr int U = 6;  // three streams in
@@ -276,10 +279,20 @@ __global__ void __launch_bounds__(BT, BPS) bicg_p_kernel(int64_t N, const T* __r
         if (!first) vp[u] = p[i], vv[u] = v[i];
       }
     }
+    T vi[U];
+    if (sp) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (base + u * BT < N) vi[u] = inv[base + u * BT];
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t i = base + u * BT;
-      if (i < N) p[i] = first ? vr[u] : (T)((double)vr[u] + beta * ((double)vp[u] - om * (double)vv[u]));
+      if (i < N) {
+        const T pv = first ? vr[u] : (T)((double)vr[u] + beta * ((double)vp[u] - om * (double)vv[u]));
+        p[i] = pv;
+        if (sp) sp[i] = vi[u] * pv;
+      }
     }
   }
 }
@@ -287,7 +300,8 @@ __global__ void __launch_bounds__(BT, BPS) bicg_p_kernel(int64_t N, const T* __r
 template <class T>
 __global__ void __launch_bounds__(BT, BPS) bicg_s_kernel(int64_t N, const T* __restrict__ r,
                                                          const T* __restrict__ v, T* __restrict__ s,
-                                                         const double* sc, Reduce R) {
+                                                         const double* sc, Reduce R, const T* __restrict__ inv,
+                                                         T* __restrict__ ss) {
   const double alpha = sc[SC_RHO] / sc[SC_RV];
   double d = 0.0;
   constexpr int U = 8;  // two streams in
@@ -298,12 +312,19 @@ __global__ void __launch_bounds__(BT, BPS) bicg_s_kernel(int64_t N, const T* __r
       const int64_t i = base + u * BT;
       if (i < N) vr[u] = r[i], vv[u] = v[i];
     }
+    T vi[U];
+    if (ss) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (base + u * BT < N) vi[u] = inv[base + u * BT];
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t i = base + u * BT;
       if (i < N) {
         const T sv = (T)((double)vr[u] - alpha * (double)vv[u]);
         s[i] = sv;
+        if (ss) ss[i] = vi[u] * sv;
         d += (double)sv * (double)sv;
       }
     }
@@ -599,15 +620,15 @@ ndiag_status dots(Handle* h, int nv, const T* a0, const T* b0, const T* a1, cons
 }
 
 template <class T>
-ndiag_status bicg_p(Handle* h, const T* r, T* p, const T* v, const double* sc, int first) {
-  LAUNCH((bicg_p_kernel<T>), h->N, r, p, v, sc, first);
+ndiag_status bicg_p(Handle* h, const T* r, T* p, const T* v, const double* sc, int first, const T* inv, T* sp) {
+  LAUNCH((bicg_p_kernel<T>), h->N, r, p, v, sc, first, inv, sp);
   return NDIAG_OK;
 }
 template <class T>
-ndiag_status bicg_s(Handle* h, const T* r, const T* v, T* s, double* sc) {
+ndiag_status bicg_s(Handle* h, const T* r, const T* v, T* s, double* sc, const T* inv, T* ss) {
   Reduce R = reduce_slot(h, 1);
   R.res = sc + SC_SS;
-  LAUNCH((bicg_s_kernel<T>), h->N, r, v, s, sc, R);
+  LAUNCH((bicg_s_kernel<T>), h->N, r, v, s, sc, R, inv, ss);
   return NDIAG_OK;
 }
 template <class T>
@@ -665,8 +686,8 @@ ndiag_status mul_diag(Handle* h, const T* x, T* y) {
   template ndiag_status spmv_any<T>(Handle*, const T*, T*);                                            \
   template ndiag_status dots<T>(Handle*, int, const T*, const T*, const T*, const T*, const T*,         \
                                 const T*, double*, int);                                               \
-  template ndiag_status bicg_p<T>(Handle*, const T*, T*, const T*, const double*, int);                \
-  template ndiag_status bicg_s<T>(Handle*, const T*, const T*, T*, double*);                           \
+  template ndiag_status bicg_p<T>(Handle*, const T*, T*, const T*, const double*, int, const T*, T*);  \
+  template ndiag_status bicg_s<T>(Handle*, const T*, const T*, T*, double*, const T*, T*);             \
   template ndiag_status bicg_xr<T>(Handle*, T*, const T*, const T*, T*, const T*, const T*, const T*,  \
                                    double*);                                                           \
   template ndiag_status axpy_alpha<T>(Handle*, T*, const T*, const double*);                           \

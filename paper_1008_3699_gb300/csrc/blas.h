@@ -34,8 +34,11 @@ ndiag_status residual64(Handle* h, const double* b, const double* x, double* r, 
 ndiag_status residual64_to32(Handle* h, const double* b, const double* x, float* r, double* res);
 template <class T> ndiag_status dots(Handle* h, int nv, const T* a0, const T* b0, const T* a1, const T* b1,
                                      const T* a2, const T* b2, double* res, int slot);
-template <class T> ndiag_status bicg_p(Handle* h, const T* r, T* p, const T* v, const double* sc, int first);
-template <class T> ndiag_status bicg_s(Handle* h, const T* r, const T* v, T* s, double* sc);
+// with inv and sp / ss: also sp = inv .* p, ss = inv .* s (pre-scaled sweep input)
+template <class T> ndiag_status bicg_p(Handle* h, const T* r, T* p, const T* v, const double* sc, int first,
+                                       const T* inv = nullptr, T* sp = nullptr);
+template <class T> ndiag_status bicg_s(Handle* h, const T* r, const T* v, T* s, double* sc,
+                                       const T* inv = nullptr, T* ss = nullptr);
 template <class T> ndiag_status bicg_xr(Handle* h, T* x, const T* ph, const T* sh, T* r, const T* s,
                                         const T* t, const T* rh, double* sc);
 template <class T> ndiag_status axpy_alpha(Handle* h, T* x, const T* ph, const double* sc);

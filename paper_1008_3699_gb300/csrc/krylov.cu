@@ -12,6 +12,9 @@
 namespace nd {
 
 ndiag_status do_ilu_apply(Handle* h, const void* r, void* z);
+ndiag_status do_ilu_apply_pre(Handle* h, const void* rs, void* z);
+bool ilu_prescaled_ok(const Handle* h);
+const double* ilu_pivot_inverse(const Handle* h);
 ndiag_status do_ssor_apply(Handle* h, int mode, double omega, const void* r, void* z);
 ndiag_status check_device_status(Handle* h);
 
@@ -80,6 +83,7 @@ ndiag_status apply_prec(Handle* h, const Prec& P, const void* r, void* z, size_t
 template <class T>
 struct KV {
   T *r, *rh, *p, *v, *ph, *s, *sh, *t;
+  T *ps = nullptr, *ss = nullptr;  // pivot-scaled p and s (pre-scaled ILU(0) applies)
 };
 
 // Initial residual r = b - A x for the vector type T. fp64: exact residual
@@ -121,12 +125,18 @@ ndiag_status bicgstab(Handle* h, const Prec& P, const T* b, T* x, const KV<T>& V
       ++h->launches;
       bicg_scalars_kernel<<<1, 1, 0, h->stream>>>(sc, first);
       ND_CUDA(cudaGetLastError());
-      ND_TRY(bicg_p<T>(h, V.r, V.p, V.v, sc, first));
+      // with the pre-scaled ILU(0) apply the vector kernels also write the
+      // pivot-scaled copies p / d~ and s / d~ its forward sweeps read
+      const bool pre = V.ps != nullptr;
+      const T* inv = pre ? (const T*)ilu_pivot_inverse(h) : nullptr;
+      ND_TRY(bicg_p<T>(h, V.r, V.p, V.v, sc, first, inv, V.ps));
       first = 0;
-      ND_TRY(apply_prec(h, P, V.p, V.ph, vb));
+      if (pre) ND_TRY(do_ilu_apply_pre(h, V.ps, V.ph));
+      else ND_TRY(apply_prec(h, P, V.p, V.ph, vb));
       ND_TRY(spmv_dot<T>(h, V.ph, V.v, V.rh, sc + SC_RV, 1));
-      ND_TRY(bicg_s<T>(h, V.r, V.v, V.s, sc));
-      ND_TRY(apply_prec(h, P, V.s, V.sh, vb));
+      ND_TRY(bicg_s<T>(h, V.r, V.v, V.s, sc, inv, V.ss));
+      if (pre) ND_TRY(do_ilu_apply_pre(h, V.ss, V.sh));
+      else ND_TRY(apply_prec(h, P, V.s, V.sh, vb));
       ND_TRY(spmv_dot<T>(h, V.sh, V.t, V.s, sc + SC_TS, 2, true));
       ND_TRY(bicg_xr<T>(h, x, V.ph, V.sh, V.r, V.s, V.t, V.rh, sc));
       ND_TRY(pull(h));
@@ -305,7 +315,7 @@ extern "C" ndiag_status krylov_solve(ndiag* h, int method, int precond, int mode
   const bool fp64 = h->precision == NDIAG_FP64;
   const bool dev_b = is_device_ptr(b), dev_x = is_device_ptr(x);
   // fp64 vectors: 8 Krylov + alt + b copy + x copy ; fp32: 8 inner + e + r64 + b + x
-  const size_t need = fp64 ? v64 * 11 : v32 * 9 + v64 * 3;
+  const size_t need = fp64 ? v64 * 13 : v32 * 9 + v64 * 3;  // fp64: + the two pre-scaled vectors
   ND_TRY(ensure_kws(h, need));
   char* cur = (char*)h->kws.p;
   Prec P{precond, mode, omega[0]};
@@ -314,6 +324,11 @@ extern "C" ndiag_status krylov_solve(ndiag* h, int method, int precond, int mode
   double bnorm = 0.0, relres = 0.0;
   if (fp64) {
     KV<double> V = carve<double>(cur, N);
+    if (method == NDIAG_BICGSTAB && precond == NDIAG_PREC_ILU0 && ilu_prescaled_ok(h)) {
+      V.ps = (double*)cur;
+      V.ss = (double*)(cur + v64);
+    }
+    cur += 2 * v64;
     double* xalt = (double*)cur;
     cur += v64;
     double* bd = dev_b ? (double*)b : (double*)cur;
