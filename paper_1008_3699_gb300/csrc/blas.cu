@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(BT, BPS) bicg_p_kernel(int64_t N, const T* __r
                                                          const T* __restrict__ inv, T* __restrict__ sp) {
   const double rho = sc[SC_RHO], rho_old = sc[SC_RHO_OLD], alpha = sc[SC_ALPHA], om = sc[SC_OM];
   const double beta = first ? 0.0 : (rho / rho_old) * (alpha / om);
-  constexpr int U = 6;  // three streams in
+  constexpr int U = 4;  // three or four streams in
   ND_STREAM_LOOP(N) {
     T vr[U], vp[U], vv[U];
 #pragma unroll
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(BT, BPS) bicg_s_kernel(int64_t N, const T* __r
                                                          T* __restrict__ ss) {
   const double alpha = sc[SC_RHO] / sc[SC_RV];
   double d = 0.0;
-  constexpr int U = 8;  // two streams in
+  constexpr int U = 4;  // two or three streams in
   ND_STREAM_LOOP(N) {
     T vr[U], vv[U];
 #pragma unroll
