@@ -180,7 +180,7 @@ __device__ __forceinline__ T cell9(const P9<T, TC>& P, const Sub9& S, T* tw, int
     const T piv = M[k][k];
 #pragma unroll
     for (int i = k + 1; i < n; ++i) {
-      const T f = M[i][k] / piv;
+      const T f = k == 0 ? M[i][k] : M[i][k] / piv;  // row 0 keeps its unit pivot
       if (f != T(0)) {
 #pragma unroll
         for (int j = k + 1; j < n; ++j) M[i][j] = fma(-f, M[k][j], M[i][j]);
@@ -194,7 +194,7 @@ __device__ __forceinline__ T cell9(const P9<T, TC>& P, const Sub9& S, T* tw, int
     T s = hv[k];
 #pragma unroll
     for (int j = k + 1; j < n; ++j) s = fma(-M[k][j], xs[j], s);
-    xs[k] = s / M[k][k];
+    xs[k] = k == 0 ? s : s / M[k][k];
   }
 #pragma unroll
   for (int m = 0; m < n; ++m) {
