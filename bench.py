@@ -178,7 +178,7 @@ def main():
     ap.add_argument("--kernel-only", type=int, default=0, metavar="K",
                     help="only factor and run K ILU(0) applies of the workload (for kernel profiling)")
     ap.add_argument("--workload", default="varcoef2048",
-                    choices=["varcoef2048", "poisson64", "poisson3d", "batch512", "serving"],
+                    choices=["varcoef2048", "poisson64", "poisson3d", "batch512", "serving", "mg2048"],
                     help="varcoef2048 is the benchmark; the others print one measurement line each")
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--n3d", type=int, default=256, help="side of the 3D Poisson workload (subdomains of 32^3)")
@@ -537,8 +537,64 @@ def workload_serving(args):
                           "peak_kind": kind, "kernel": "sweep9_kernel (ILU(0) forward and backward, fp64)"}}}))
 
 
+def workload_mg2048(args):
+    """The 2048^2 variable-coefficient workload (16 x 16 subdomains) solved by
+    PCG with one multigrid V-cycle per iteration, the decomposed SSOR apply
+    (omega 0.9) smoothing every level; beside it one BiCGSTAB + decomposed
+    ILU(0) solve of the same system. V-cycle time with CUDA events around whole
+    cycles."""
+    import numpy as np
+    torch, nd, W = _setup()
+    p = W.varcoef2d_problem()
+    n, om = p["n"][0], 0.9
+    h = nd.NDiag(2, p["n"], 5, p["diags"], p["sub"], "fp64")
+    b = torch.tensor(p["b"], device="cuda")
+    r = b.clone()
+    z = torch.empty_like(r)
+    for _ in range(max(3, args.warmup)):
+        h.mg_apply(om, r, z)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(10):
+        h.mg_apply(om, r, z)
+    e1.record()
+    torch.cuda.synchronize()
+    vc_ms = e0.elapsed_time(e1) / 10
+    levels = h.mg_levels()
+    # algorithmic bytes of one cycle, per cell of a level: two SSOR applies
+    # (forward: pivot, 2 entries, r, tmp; backward: 2 entries, tmp, z) = 2 x 72,
+    # two residuals (5 entries, b, x, r) = 2 x 64, restriction 10, prolongation
+    # 18, the post-smoothing add 24; the coarsest level: 4 applies, 3 residuals,
+    # 3 adds
+    sizes, nx, ny = [], n, n
+    for _ in range(levels):
+        sizes.append(nx * ny)
+        nx, ny = (nx + 1) // 2, (ny + 1) // 2
+    vc_bytes = sum(c * 324 for c in sizes[:-1]) + sizes[-1] * (4 * 72 + 3 * 64 + 3 * 24)
+    peak, kind = measured_peaks()
+    gbs = vc_bytes / (vc_ms / 1e3) / 1e9
+    walls = []
+    for k in range(args.warmup + max(1, args.steps)):
+        x = torch.zeros_like(b)
+        info = _timed_solve(torch, h, nd.PCG, nd.PREC_MG, b, x, rtol=1e-8, maxit=2000, omega=om)
+        if k >= args.warmup:
+            walls.append(info["wall_s"])
+    h.ilu0_factor()
+    x = torch.zeros_like(b)
+    ilu = _timed_solve(torch, h, nd.BICGSTAB, nd.PREC_ILU0, b, x, rtol=1e-8, maxit=20000)
+    h.close()
+    print(json.dumps({"workload": f"varcoef2d-{n}x{n}-5pt-fp64-mg-pcg-16x16", "metric": "solve seconds to rel-res 1e-8",
+                      "mg_pcg": {"iters": info["iters"], "relres": info["relres"], "wall_s": float(np.median(walls)),
+                                 "levels": levels, "omega": om, "vcycle_ms": vc_ms},
+                      "vcycle_roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                          "frac": gbs / peak, "peak_kind": kind,
+                                          "kernel": "one V-cycle (sweep2d SSOR applies, residuals, transfers)"},
+                      "bicgstab_ilu0": {k: ilu[k] for k in ("iters", "relres", "wall_s")}}))
+
+
 EXTRA = {"poisson64": workload_poisson64, "poisson3d": workload_poisson3d,
-         "batch512": workload_batch512, "serving": workload_serving}
+         "batch512": workload_batch512, "serving": workload_serving, "mg2048": workload_mg2048}
 
 
 if __name__ == "__main__":

@@ -66,7 +66,7 @@ enum {
 };
 
 enum { NDIAG_PCG = 0, NDIAG_BICGSTAB = 1, NDIAG_STATIONARY = 2 };
-enum { NDIAG_PREC_NONE = 0, NDIAG_PREC_SSOR = 1, NDIAG_PREC_ILU0 = 2 };
+enum { NDIAG_PREC_NONE = 0, NDIAG_PREC_SSOR = 1, NDIAG_PREC_ILU0 = 2, NDIAG_PREC_MG = 3 };
 
 /* Optional device allocator (e.g. a framework's caching allocator). Without
  * one the library calls cudaMallocAsync / cudaFreeAsync on its stream. */
@@ -132,6 +132,32 @@ ndiag_status sor_sweep(ndiag* h, int mode, const double* omega, int64_t t, const
 ndiag_status ssor_apply(ndiag* h, int mode, double omega, const void* r, void* z);
 
 /*
+ * mg_apply -- one multigrid V-cycle z = B r with the decomposed SSOR apply as
+ * smoother on every level (the sweep used as a multigrid smoother, Sec. 5,
+ * opening paragraph), the preconditioner that krylov_solve runs for
+ * NDIAG_PREC_MG. On level k (level 0 = this handle):
+ *     z  = S_k r
+ *     z += 1.8 P_k B_{k+1} P_k^T (r - A_k z)
+ *     z += S_k (r - A_k z)
+ * S_k = ssor_apply(DECOMPOSED, omega) of level k; P_k = piecewise-constant
+ * prolongation over 2 x 2 cell aggregates (x // 2, y // 2); A_{k+1} =
+ * P_k^T A_k P_k (5-point again), split into ceil(nx/128) x ceil(ny/128)
+ * subdomains; coarsening stops when both sides are <= 32 cells or at 10
+ * levels; the coarsest level takes 4 steps of SSOR-Richardson. B is symmetric;
+ * it is positive definite when S contracts in the A-norm, which for subdomains
+ * meeting at interior vertices needs omega < 1.
+ *   r, z  fp64 DEVICE vectors of N values, z must not alias r.
+ * The first call builds the hierarchy on the host from the handle's matrix
+ * (a blocking device-to-host copy), later calls are asynchronous.
+ * Errors: NDIAG_EINVAL (not a 2D 5-point fp64 handle, omega outside (0, 2)),
+ * NDIAG_ENOMEM.
+ */
+ndiag_status mg_apply(ndiag* h, double omega, const double* r, double* z);
+
+/* Levels of the handle's multigrid hierarchy (0 before the first MG use). */
+int ndiag_mg_levels(const ndiag* h);
+
+/*
  * ilu0_factor -- ILU(0) (Sec. 5: one symmetric Gauss-Seidel pass on an
  * n-diagonal matrix is ILU(0)). DECOMPOSED: M = (D~ + L_J) D~^-1 (D~ + U_J),
  * L_J / U_J = implicit entries of the forward phase / of its reverse, and
@@ -186,7 +212,17 @@ typedef struct {
  * krylov_solve -- solve A x = b to ||b - A x||_2 / ||b||_2 <= rtol.
  *   method  NDIAG_PCG, NDIAG_BICGSTAB or NDIAG_STATIONARY (SOR sweeps of the
  *           schedule t = 0, 1, 2, ..., omega[] per direction).
- *   precond NDIAG_PREC_NONE / SSOR / ILU0 (ignored for STATIONARY).
+ *   precond NDIAG_PREC_NONE / SSOR / ILU0 / MG (ignored for STATIONARY).
+ *           MG: one symmetric multigrid V-cycle with the decomposed SSOR apply
+ *           (factor omega[0]) as pre- and post-smoother on every level (the
+ *           sweep as a multigrid smoother, Sec. 5). Coarse levels are the
+ *           Galerkin products P^T A P over 2 x 2 cell aggregates
+ *           (piecewise-constant P, so every level stays 5-point), down to a
+ *           grid of at most 32 cells per side, where 4 SSOR steps are taken.
+ *           2D 5-point fp64 handles and DECOMPOSED mode only (else
+ *           NDIAG_EINVAL). The hierarchy is built on the host from the
+ *           handle's matrix on the first MG solve, kept on the handle and
+ *           freed by ndiag_destroy.
  *   mode    NDIAG_DECOMPOSED or NDIAG_NATURAL ordering of the sweeps.
  *   omega   HOST array of 2^dim relaxation factors (STATIONARY), omega[0] is
  *           the SSOR factor.

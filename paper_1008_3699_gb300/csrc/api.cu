@@ -367,6 +367,7 @@ ndiag_status ndiag_create(ndiag** out, int dim, const int64_t n[3], int stencil,
 void ndiag_destroy(ndiag* h) {
   if (!h) return;
   cudaStream_t s = h->stream;
+  mg_free(h);
   dev_free(h->A64, 0, s);
   dev_free(h->Alo, 0, s);
   dev_free(h->sor.base, h->sor.bytes, s);

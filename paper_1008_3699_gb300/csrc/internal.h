@@ -90,6 +90,8 @@ struct ProfRec {
   double bytes = 0.0;
 };
 
+struct Multigrid;  // mg.cu
+
 struct Handle {
   int dim = 0, stencil = 0, precision = 0;
   int64_t n[3] = {1, 1, 1};
@@ -132,6 +134,7 @@ struct Handle {
   bool profiling = false;
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> ev_pool;
+  Multigrid* mg = nullptr;       // V-cycle hierarchy (built on the first multigrid apply)
 };
 
 // Sweep-launch timing: brackets a sweep kernel with events when profiling is
@@ -223,6 +226,12 @@ ndiag_status build_scaled_transposed(Handle* h, ScaledSet& set);
 ndiag_status spmv64(Handle* h, const double* x, double* y);
 ndiag_status residual64(Handle* h, const double* b, const double* x, double* r, double* norm2_dev);
 int reduce_blocks(const Handle* h);
+
+// Multigrid V-cycle preconditioner (mg.cu): z = B r on a 2D 5-point fp64
+// handle; the hierarchy is built on the first call and freed by mg_free.
+ndiag_status mg_apply(Handle* h, double omega, const double* r, double* z);
+ndiag_status mg_check(Handle* h);  // device status of the coarse levels
+void mg_free(Handle* h);
 
 }  // namespace nd
 

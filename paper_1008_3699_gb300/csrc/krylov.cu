@@ -76,6 +76,7 @@ struct Prec {
 ndiag_status apply_prec(Handle* h, const Prec& P, const void* r, void* z, size_t bytes) {
   if (P.kind == NDIAG_PREC_ILU0) return do_ilu_apply(h, r, z);
   if (P.kind == NDIAG_PREC_SSOR) return do_ssor_apply(h, P.mode, P.omega, r, z);
+  if (P.kind == NDIAG_PREC_MG) return mg_apply(h, P.omega, (const double*)r, (double*)z);
   ND_CUDA(cudaMemcpyAsync(z, r, bytes, cudaMemcpyDeviceToDevice, h->stream));
   return NDIAG_OK;
 }
@@ -303,7 +304,13 @@ extern "C" ndiag_status krylov_solve(ndiag* h, int method, int precond, int mode
   const auto t0 = std::chrono::steady_clock::now();
   if (!h || !b || !x || !omega || !(rtol > 0.0) || maxit < 0) return NDIAG_EINVAL;
   if (method < NDIAG_PCG || method > NDIAG_STATIONARY) return NDIAG_EINVAL;
-  if (precond < NDIAG_PREC_NONE || precond > NDIAG_PREC_ILU0) return NDIAG_EINVAL;
+  if (precond < NDIAG_PREC_NONE || precond > NDIAG_PREC_MG) return NDIAG_EINVAL;
+  if (method != NDIAG_STATIONARY && precond == NDIAG_PREC_MG &&
+      (h->dim != 2 || h->stencil != 5 || h->precision != NDIAG_FP64 || mode != NDIAG_DECOMPOSED ||
+       !(omega[0] > 0.0 && omega[0] < 2.0))) {
+    set_error("the multigrid preconditioner needs a 2D 5-point fp64 handle, DECOMPOSED mode and 0 < omega < 2");
+    return NDIAG_EINVAL;
+  }
   if (mode != NDIAG_NATURAL && mode != NDIAG_DECOMPOSED) return NDIAG_EINVAL;
   if (method != NDIAG_STATIONARY && precond == NDIAG_PREC_ILU0 && h->ilu_mode < 0) {
     set_error("ILU(0) preconditioner requested before ilu0_factor");
@@ -406,7 +413,8 @@ extern "C" ndiag_status krylov_solve(ndiag* h, int method, int precond, int mode
     if (!dev_x) ND_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
   }
   ND_CUDA(cudaStreamSynchronize(h->stream));
-  const ndiag_status ds = check_device_status(h);
+  ndiag_status ds = check_device_status(h);
+  if (ds == NDIAG_OK && P.kind == NDIAG_PREC_MG && method != NDIAG_STATIONARY) ds = mg_check(h);
   if (ds != NDIAG_OK) st = ds;
   if (info) {
     info->iterations = iters;

@@ -22,11 +22,11 @@ FP64, FP32, FP32_D16 = 0, 1, 2
 PRECISION = {"fp64": FP64, "fp32": FP32, "fp32_d16": FP32_D16}
 NATURAL, DECOMPOSED = 0, 1
 PCG, BICGSTAB, STATIONARY = 0, 1, 2
-PREC_NONE, PREC_SSOR, PREC_ILU0 = 0, 1, 2
+PREC_NONE, PREC_SSOR, PREC_ILU0, PREC_MG = 0, 1, 2, 3
 
 # every symbol include/ndiag.h declares
 EXPORTED = ["ndiag_set_allocator", "ndiag_last_error", "ndiag_create", "ndiag_destroy", "ndiag_cells",
-            "ndiag_precision", "sor_sweep", "ssor_apply", "ilu0_factor", "ilu0_apply", "ndiag_residual",
+            "ndiag_precision", "sor_sweep", "ssor_apply", "mg_apply", "ndiag_mg_levels", "ilu0_factor", "ilu0_apply", "ndiag_residual",
             "krylov_solve", "ndiag_tune_omega", "ndiag_profile", "ndiag_read_counters", "ilu0_apply_noalloc",
             "ndiag_batch_create", "ndiag_batch_autotune", "ndiag_batch_tiles", "ndiag_batch_solve",
             "ndiag_batch_cells", "ndiag_batch_launches", "ndiag_batch_destroy",
@@ -95,6 +95,8 @@ def load(path: str = LIB_PATH):
     L.ndiag_precision.argtypes = [P]
     L.sor_sweep.argtypes = [P, I, P, L64, P, P, P]
     L.ssor_apply.argtypes = [P, I, D, P, P]
+    L.mg_apply.argtypes = [P, D, P, P]
+    L.ndiag_mg_levels.argtypes = [P]
     L.ilu0_factor.argtypes = [P, I]
     L.ilu0_apply.argtypes = [P, P, P]
     L.ilu0_apply_noalloc.argtypes = [P, P, P]
@@ -210,6 +212,13 @@ class NDiag:
 
     def ssor_apply(self, omega, r, z, mode=DECOMPOSED):
         _check(self.L, self.L.ssor_apply(self.h, mode, float(omega), _ptr(r), _ptr(z)))
+
+    def mg_apply(self, omega, r, z):
+        """One multigrid V-cycle z = B r (fp64 device tensors)."""
+        _check(self.L, self.L.mg_apply(self.h, float(omega), _ptr(r), _ptr(z)))
+
+    def mg_levels(self):
+        return int(self.L.ndiag_mg_levels(self.h))
 
     def ilu0_factor(self, mode=DECOMPOSED):
         _check(self.L, self.L.ilu0_factor(self.h, mode))
