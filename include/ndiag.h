@@ -141,8 +141,8 @@ ndiag_status ssor_apply(ndiag* h, int mode, double omega, const void* r, void* z
  *     z += S_k (r - A_k z)
  * S_k = ssor_apply(DECOMPOSED, omega) of level k; P_k = piecewise-constant
  * prolongation over 2 x 2 cell aggregates (x // 2, y // 2); A_{k+1} =
- * P_k^T A_k P_k (5-point again), split into ceil(nx/128) x ceil(ny/128)
- * subdomains; coarsening stops when both sides are <= 32 cells or at 10
+ * P_k^T A_k P_k (5-point again), split into min(16, max(1, nx / 16)) x
+ * min(16, max(1, ny / 16)) subdomains; coarsening stops when both sides are <= 32 cells or at 10
  * levels; the coarsest level takes 4 steps of SSOR-Richardson. B is symmetric;
  * it is positive definite when S contracts in the A-norm, which for subdomains
  * meeting at interior vertices needs omega < 1.

@@ -15,7 +15,8 @@ cycle used as a PCG preconditioner, written in the plainest form:
              cell wide). A_{k+1} keeps the 5-point pattern. Coarsening stops once
              both sides are at most 32 cells, or after 10 levels.
   partition  level 0 keeps the caller's subdomains; a coarse level of
-             nx x ny cells is split into ceil(nx/128) x ceil(ny/128).
+             nx x ny cells is split into min(16, max(1, nx // 16)) x
+             min(16, max(1, ny // 16)) subdomains.
   smoother   S_k = the decomposed SSOR apply of level k (Sec. 2: SSOR = a sweep
              and its reverse, in the SPD form), factor omega.
   cycle      B_k r:  z  = S_k r
@@ -54,7 +55,10 @@ KC = 4          # SSOR-Richardson steps on the coarsest level
 ALPHA = 1.8     # over-correction of the coarse-grid correction
 NMIN = 32       # coarsen while a side exceeds this
 LMAX = 10       # levels at most
-COARSE_SUB = 128  # target subdomain side on coarse levels
+
+def coarse_parts(n: int) -> int:
+    """Subdomains along an axis of n cells on a coarse level."""
+    return min(16, max(1, n // 16))
 
 
 def prolongation(nx: int, ny: int) -> sp.csr_matrix:
@@ -114,7 +118,7 @@ class Hierarchy:
         while (nx > NMIN or ny > NMIN) and len(self.levels) < LMAX:
             d = galerkin(nx, ny, d)
             nx, ny = (nx + 1) // 2, (ny + 1) // 2
-            sub_c = (max(1, math.ceil(nx / COARSE_SUB)), max(1, math.ceil(ny / COARSE_SUB)))
+            sub_c = (coarse_parts(nx), coarse_parts(ny))
             self.levels.append((nx, ny, oracle.Problem(2, (nx, ny), 5, d, sub_c, library=library)))
 
     def smooth(self, k, r):

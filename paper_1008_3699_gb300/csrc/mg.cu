@@ -149,7 +149,9 @@ ndiag_status mg_build(Handle* h) {
     L.ny = nyc;
     L.vb = sizeof(double) * (size_t)nxc * nyc;
     const int64_t n[3] = {nxc, nyc, 1};
-    const int sub[3] = {std::max(1, (nxc + 127) / 128), std::max(1, (nyc + 127) / 128), 1};
+    // at least 16 cells a side, at most 16 parts an axis: the sequential
+    // path of a coarse sweep stays short while the smoother keeps its quality
+    const int sub[3] = {std::min(16, std::max(1, nxc / 16)), std::min(16, std::max(1, nyc / 16)), 1};
     ndiag* hc = nullptr;
     ND_TRY(ndiag_create(&hc, 2, n, 5, C.data(), sub, NDIAG_FP64, h->stream));
     L.h = hc;

@@ -9,9 +9,9 @@
 // in the reversed frame, without twins, leaving out the start lines that border
 // coupled interfaces). The coupled pairs along an interface depend on the
 // interior cells of both subdomains and are solved afterwards, from the far
-// end of the interface back to its start vertex, one thread per interface;
+// end of the interface back to its start vertex, one warp per interface;
 // the four start corners at a vertex form the 4x4 system of Eq. (2d:sor4b4),
-// solved by whichever of the vertex's four interface threads finishes last
+// solved by whichever of the vertex's four interface chains finishes last
 // (arrival counter, no waiting).
 #include <algorithm>
 #include <cstring>
@@ -46,13 +46,6 @@ struct EdgeP {
 template <class T, class TC>
 __device__ __forceinline__ T coef(const EdgeP<T, TC>& P, int e, int64_t i) {
   return P.om * ldc<T, TC>(P.cT[e] + i);
-}
-
-template <class T>
-__device__ __forceinline__ void pair_solve(T ha, T gab, T hb, T gba, T& xa, T& xb) {
-  const T det = fma(-gab, gba, T(1));
-  xa = fma(-gab, hb, ha) / det;
-  xb = fma(-gba, ha, hb) / det;
 }
 
 template <class T>
@@ -100,12 +93,64 @@ __device__ void solve_vertex(const EdgeP<T, TC>& P, int vx, int vy) {
   for (int k = 0; k < 4; ++k) P.z[idx[k]] = xx[k];
 }
 
+// Chains are run by one warp each: lanes load the inputs of 32 consecutive
+// pairs at once (right-hand side, the interior neighbour terms, the couplings
+// and 1/det of every 2x2 pair system), then lane 0 runs the recurrence over
+// them, three dependent operations a pair, and the warp stores the results.
+constexpr int ELN = 32;            // lanes per chain
+constexpr int ETH = 128;           // threads per block: 4 chains
+constexpr int ECH = ETH / ELN;
+
+// per-warp staging of one chunk of a chain
+template <class T>
+struct Chunk {
+  T hp[ELN], hq[ELN], a[ELN], b[ELN], gab[ELN], gba[ELN], idet[ELN];
+};
+
+// Pair k of a chain (k = 0 at the far end): cells ip, iq of the pair, the
+// entries towards the previous pair (k - 1), between the two cells, and the
+// interior neighbour terms, staged into slot j of the chunk.
 template <class T, class TC>
-__device__ __forceinline__ void edges_body(const EdgeP<T, TC>& P, int id) {
+__device__ __forceinline__ void stage_pair(const EdgeP<T, TC>& P, const TC* const (&c)[5], Chunk<T>& C, int j,
+                                           int k, int64_t ip, int64_t iq, int64_t dip, int64_t diq, bool in_p,
+                                           bool in_q) {
+  T hp = __ldcg(P.w + ip), hq = __ldcg(P.w + iq);
+  if (in_p) hp = fma(-(P.om * ldc<T, TC>(c[3] + ip)), __ldcg(P.z + ip + dip), hp);
+  if (in_q) hq = fma(-(P.om * ldc<T, TC>(c[4] + iq)), __ldcg(P.z + iq + diq), hq);
+  const T gab = P.om * ldc<T, TC>(c[1] + ip), gba = P.om * ldc<T, TC>(c[2] + iq);
+  C.hp[j] = hp;
+  C.hq[j] = hq;
+  C.a[j] = k > 0 ? P.om * ldc<T, TC>(c[0] + ip) : T(0);
+  C.b[j] = k > 0 ? P.om * ldc<T, TC>(c[0] + iq) : T(0);
+  C.gab[j] = gab;
+  C.gba[j] = gba;
+  C.idet[j] = T(1) / fma(-gab, gba, T(1));
+}
+
+// Lane 0: pairs j < m of the chunk, in chain order; results replace hp / hq.
+template <class T>
+__device__ __forceinline__ void run_chunk(Chunk<T>& C, int m, T& zp, T& zq) {
+#pragma unroll 4
+  for (int j = 0; j < m; ++j) {
+    const T hp = fma(-C.a[j], zp, C.hp[j]);
+    const T hq = fma(-C.b[j], zq, C.hq[j]);
+    zp = fma(-C.gab[j], hq, hp) * C.idet[j];
+    zq = fma(-C.gba[j], hp, hq) * C.idet[j];
+    C.hp[j] = zp;
+    C.hq[j] = zq;
+  }
+}
+
+template <class T, class TC>
+__device__ __forceinline__ void edges_body(const EdgeP<T, TC>& P, int id, int lane, Chunk<T>& C) {
   const int px = P.sx.p, py = P.sy.p;
   const int ny_tasks = px * (py - 1), nx_tasks = (px - 1) * py;
   if (id >= ny_tasks + nx_tasks) return;
   int vx = -1, vy = -1;
+  // chain geometry: first cell of pair k is ip(k) = i0 - k * step, second iq = ip + dq
+  int64_t i0 = 0, step = 0, dq = 0, dip = 0, diq = 0;
+  int npairs = 0, en = 0, eab = 0, eba = 0, eip = 0, eiq = 0;
+  bool in_p = false, in_q = false;
   if (id < ny_tasks) {
     // interface between (ix, iy) below and (ix, iy+1) above; pairs along x
     const int ix = id % px, iy = id / px;
@@ -114,7 +159,8 @@ __device__ __forceinline__ void edges_body(const EdgeP<T, TC>& P, int id) {
     const int cx = c & 1;
     const int gx0 = P.sx.lo(ix), w = P.sx.len(ix);
     const int Y = P.sy.lo(iy) + P.sy.len(iy) - 1;
-    const bool in_p = P.sy.len(iy) >= 2, in_q = P.sy.len(iy + 1) >= 2;
+    in_p = P.sy.len(iy) >= 2;
+    in_q = P.sy.len(iy + 1) >= 2;
     const int dx = cx ? -1 : 1;
     const int ge = cx ? gx0 : gx0 + w - 1;  // far end of the chain
     const bool corner = cx ? (gx0 + w < P.nx) : (gx0 > 0);
@@ -122,28 +168,18 @@ __device__ __forceinline__ void edges_body(const EdgeP<T, TC>& P, int id) {
       vx = cx ? ix : ix - 1;
       vy = iy;
     }
-    // pairs from the far end back to the start; the start column belongs to
-    // the corner system when there is one
-    const int npairs = corner ? w - 1 : w;
-    T zp_next = T(0), zq_next = T(0);
-    for (int k = 0; k < npairs; ++k) {
-      const int gx = ge - k * dx;
-      const int64_t ip = (int64_t)Y * P.nx + gx, iq = ip + P.nx;
-      T hp = __ldcg(P.w + ip), hq = __ldcg(P.w + iq);
-      const int en = cx ? 0 : 1;  // entry towards the next cell along the chain
-      if (gx != ge) {
-        hp = fma(-coef(P, en, ip), zp_next, hp);
-        hq = fma(-coef(P, en, iq), zq_next, hq);
-      }
-      if (in_p) hp = fma(-coef(P, 2, ip), __ldcg(P.z + ip - P.nx), hp);
-      if (in_q) hq = fma(-coef(P, 3, iq), __ldcg(P.z + iq + P.nx), hq);
-      T zp, zq;
-      pair_solve(hp, coef(P, 3, ip), hq, coef(P, 2, iq), zp, zq);
-      P.z[ip] = zp;
-      P.z[iq] = zq;
-      zp_next = zp;
-      zq_next = zq;
-    }
+    // the start column belongs to the corner system when there is one
+    npairs = corner ? w - 1 : w;
+    i0 = (int64_t)Y * P.nx + ge;
+    step = dx;
+    dq = P.nx;
+    en = cx ? 0 : 1;  // entry towards the previous pair along the chain
+    eab = 3;
+    eba = 2;
+    eip = 2;
+    dip = -P.nx;
+    eiq = 3;
+    diq = P.nx;
   } else {
     // interface between (ix, iy) left and (ix+1, iy) right; pairs along y
     const int k = id - ny_tasks;
@@ -153,7 +189,8 @@ __device__ __forceinline__ void edges_body(const EdgeP<T, TC>& P, int id) {
     const int cy = (c >> 1) & 1;
     const int gy0 = P.sy.lo(iy), h = P.sy.len(iy);
     const int X = P.sx.lo(ix) + P.sx.len(ix) - 1;
-    const bool in_p = P.sx.len(ix) >= 2, in_q = P.sx.len(ix + 1) >= 2;
+    in_p = P.sx.len(ix) >= 2;
+    in_q = P.sx.len(ix + 1) >= 2;
     const int dy = cy ? -1 : 1;
     const int ge = cy ? gy0 : gy0 + h - 1;
     const bool corner = cy ? (gy0 + h < P.ny) : (gy0 > 0);
@@ -161,34 +198,43 @@ __device__ __forceinline__ void edges_body(const EdgeP<T, TC>& P, int id) {
       vx = ix;
       vy = cy ? iy : iy - 1;
     }
-    const int npairs = corner ? h - 1 : h;
-    T zp_next = T(0), zq_next = T(0);
-    for (int k = 0; k < npairs; ++k) {
-      const int gy = ge - k * dy;
-      const int64_t ip = (int64_t)gy * P.nx + X, iq = ip + 1;
-      T hp = __ldcg(P.w + ip), hq = __ldcg(P.w + iq);
-      const int en = cy ? 2 : 3;
-      if (gy != ge) {
-        hp = fma(-coef(P, en, ip), zp_next, hp);
-        hq = fma(-coef(P, en, iq), zq_next, hq);
-      }
-      if (in_p) hp = fma(-coef(P, 0, ip), __ldcg(P.z + ip - 1), hp);
-      if (in_q) hq = fma(-coef(P, 1, iq), __ldcg(P.z + iq + 1), hq);
-      T zp, zq;
-      pair_solve(hp, coef(P, 1, ip), hq, coef(P, 0, iq), zp, zq);
-      P.z[ip] = zp;
-      P.z[iq] = zq;
-      zp_next = zp;
-      zq_next = zq;
+    npairs = corner ? h - 1 : h;
+    i0 = (int64_t)ge * P.nx + X;
+    step = (int64_t)dy * P.nx;
+    dq = 1;
+    en = cy ? 2 : 3;
+    eab = 1;
+    eba = 0;
+    eip = 0;
+    dip = -1;
+    eiq = 1;
+    diq = 1;
+  }
+  const TC* const c[5] = {P.cT[en], P.cT[eab], P.cT[eba], P.cT[eip], P.cT[eiq]};
+  T zp = T(0), zq = T(0);
+  for (int k0 = 0; k0 < npairs; k0 += ELN) {
+    const int k = k0 + lane;
+    const int64_t ip = i0 - (int64_t)k * step, iq = ip + dq;
+    if (k < npairs) stage_pair(P, c, C, lane, k, ip, iq, dip, diq, in_p, in_q);
+    __syncwarp();
+    if (lane == 0) run_chunk(C, min(ELN, npairs - k0), zp, zq);
+    __syncwarp();
+    if (k < npairs) {
+      P.z[ip] = C.hp[lane];
+      P.z[iq] = C.hq[lane];
     }
+    __syncwarp();
   }
   if (vx >= 0) {
-    __threadfence();
-    const unsigned vid = (unsigned)(vx + (px - 1) * vy);
-    if (atomicAdd(&P.vcount[vid], 1u) == 3u) {
-      P.vcount[vid] = 0;  // ready for the next apply
-      __threadfence();
-      solve_vertex(P, vx, vy);
+    __threadfence();  // every lane's chain values before the arrival
+    __syncwarp();
+    if (lane == 0) {
+      const unsigned vid = (unsigned)(vx + (px - 1) * vy);
+      if (atomicAdd(&P.vcount[vid], 1u) == 3u) {
+        P.vcount[vid] = 0;  // ready for the next apply
+        __threadfence();
+        solve_vertex(P, vx, vy);
+      }
     }
   }
 }
@@ -219,22 +265,26 @@ __global__ void transposed_set_kernel(int nx, int ny, int nz, int s, int64_t N, 
 }
 
 template <class T, class TC>
-__global__ void ssor_edges_kernel(EdgeP<T, TC> P) {
-  edges_body(P, blockIdx.x * blockDim.x + threadIdx.x);
+__global__ void __launch_bounds__(ETH) ssor_edges_kernel(EdgeP<T, TC> P) {
+  __shared__ Chunk<T> C[ECH];
+  const int wid = threadIdx.x / ELN;
+  edges_body(P, blockIdx.x * ECH + wid, threadIdx.x % ELN, C[wid]);
 }
 
 // The interface chains of several problems: problem p owns blocks
-// off[p] .. off[p+1] - 1 (64 threads each).
+// off[p] .. off[p+1] - 1 (ECH chains each).
 template <class T, class TC>
-__global__ void ssor_edges_batch_kernel(const EdgeP<T, TC>* __restrict__ Pa, const unsigned* __restrict__ off,
-                                        int np) {
+__global__ void __launch_bounds__(ETH) ssor_edges_batch_kernel(const EdgeP<T, TC>* __restrict__ Pa,
+                                                              const unsigned* __restrict__ off, int np) {
+  __shared__ Chunk<T> C[ECH];
   int lo = 0, hi = np - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (off[mid] <= blockIdx.x) lo = mid;
     else hi = mid - 1;
   }
-  edges_body(Pa[lo], (int)(blockIdx.x - off[lo]) * blockDim.x + threadIdx.x);
+  const int wid = threadIdx.x / ELN;
+  edges_body(Pa[lo], (int)(blockIdx.x - off[lo]) * ECH + wid, threadIdx.x % ELN, C[wid]);
 }
 
 template <class T, class TC>
@@ -274,7 +324,7 @@ ndiag_status run_edges(Handle* h, int mode, double omega, const void* w, void* z
   ND_TRY(edge_params(h, omega, w, z, P, tasks));
   if (tasks <= 0) return NDIAG_OK;
   ++h->launches;
-  ssor_edges_kernel<T, TC><<<(tasks + 63) / 64, 64, 0, h->stream>>>(P);
+  ssor_edges_kernel<T, TC><<<(tasks + ECH - 1) / ECH, ETH, 0, h->stream>>>(P);
   ND_CUDA(cudaGetLastError());
   return NDIAG_OK;
 }
@@ -287,7 +337,7 @@ ndiag_status edges_prepare_t(BatchSweep& b, Handle* const* hs, int np, double om
   for (int p = 0; p < np; ++p) {
     int tasks = 0;
     ND_TRY(edge_params(hs[p], omega, w[p], z[p], ps[p], tasks));
-    off[p + 1] = off[p] + (unsigned)((std::max(tasks, 0) + 63) / 64);
+    off[p + 1] = off[p] + (unsigned)((std::max(tasks, 0) + ECH - 1) / ECH);
   }
   const size_t pb = sizeof(EdgeP<T, TC>) * (size_t)np, ob = sizeof(unsigned) * (size_t)(np + 1);
   if (pb > b.params_bytes) {
@@ -349,10 +399,10 @@ ndiag_status batch_edges_prepare(BatchSweep& b, Handle* const* hs, int np, doubl
 ndiag_status batch_edges_launch(const BatchSweep& b, cudaStream_t s) {
   if (b.total == 0) return NDIAG_OK;
   if (b.precision == NDIAG_FP64)
-    ssor_edges_batch_kernel<double, double><<<b.total, 64, 0, s>>>((const EdgeP<double, double>*)b.params, b.off,
+    ssor_edges_batch_kernel<double, double><<<b.total, ETH, 0, s>>>((const EdgeP<double, double>*)b.params, b.off,
                                                                      b.np);
   else
-    ssor_edges_batch_kernel<float, float><<<b.total, 64, 0, s>>>((const EdgeP<float, float>*)b.params, b.off, b.np);
+    ssor_edges_batch_kernel<float, float><<<b.total, ETH, 0, s>>>((const EdgeP<float, float>*)b.params, b.off, b.np);
   ND_CUDA(cudaGetLastError());
   return NDIAG_OK;
 }

@@ -39,10 +39,10 @@ def _matrix(kind, nx, ny, seed):
 
 
 CASES = [
-    (300, 260, (3, 3), 0.9, "varcoef", 41),     # 5 levels, 2 x 2 subdomains on level 1
+    (300, 260, (3, 3), 0.9, "varcoef", 41),     # 5 levels, 9 x 8 subdomains on level 1
     (257, 131, (2, 1), 0.85, "loguniform", 42),  # odd sides: one-cell-wide aggregates
     (30, 20, (2, 2), 0.9, "poisson", 43),       # one level: SSOR-Richardson only
-    (520, 64, (5, 1), 0.95, "varcoef", 44),     # elongated, 5 x 1 then 3 x 1 subdomains
+    (520, 64, (5, 1), 0.95, "varcoef", 44),     # elongated, 5 x 1 then 16 x 2 subdomains
 ]
 
 

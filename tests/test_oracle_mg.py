@@ -93,7 +93,7 @@ def test_galerkin_conserves_total():
 def test_hierarchy_shape():
     H = M.Hierarchy(300, 260, W.poisson2d(300, 260), (3, 3), 0.9)
     assert [(nx, ny) for nx, ny, _ in H.levels] == [(300, 260), (150, 130), (75, 65), (38, 33), (19, 17)]
-    assert [pb.sub[:2] for _, _, pb in H.levels] == [(3, 3), (2, 2), (1, 1), (1, 1), (1, 1)]
+    assert [pb.sub[:2] for _, _, pb in H.levels] == [(3, 3), (9, 8), (4, 4), (2, 2), (1, 1)]
     assert len(M.Hierarchy(32, 20, W.poisson2d(32, 20), (2, 2), 0.9).levels) == 1
 
 
