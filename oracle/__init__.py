@@ -55,6 +55,11 @@ def _load(path: str):
     lib.orc_fwd_phase.restype = I
     lib.orc_fwd_phase.argtypes = [I]
     lib.orc_solve.argtypes = [P, I, I, I, P, D, I, P, P, P]
+    lib.orc_eik_create.restype = P
+    lib.orc_eik_create.argtypes = [P, D, P, P]
+    lib.orc_eik_destroy.argtypes = [P]
+    lib.orc_eik_sweep.argtypes = [P, L, P, P, P]
+    lib.orc_eik_solve.argtypes = [P, P, D, I, P]
     return lib
 
 
@@ -172,6 +177,47 @@ class Problem:
         if rc:
             raise RuntimeError(f"oracle solve failed ({rc})")
         return x, dict(iters=int(info[0]), relres=float(info[1]), status=int(info[2]))
+
+
+class Eikonal:
+    """Fast sweeping for |grad u| = f on an nx x ny grid of spacing h, split
+    into sub[0] x sub[1] subdomains (decomposed Gauss-Seidel passes)."""
+
+    def __init__(self, n, h, f, sub=(1, 1), library=None):
+        self.lib = library or lib()
+        self.n = (int(n[0]), int(n[1]))
+        self.N = self.n[0] * self.n[1]
+        self.f = _f64(f).reshape(self.N)
+        n64 = np.array(self.n, dtype=np.int64)
+        sub32 = np.array(list(sub)[:2], dtype=np.int32)
+        self.h = self.lib.orc_eik_create(_ptr(n64), float(h), _ptr(self.f), _ptr(sub32))
+        if not self.h:
+            raise ValueError("oracle: bad eikonal grid/subdomains")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.lib.orc_eik_destroy(self.h)
+            self.h = None
+
+    def sweep(self, t, u_old):
+        u_old = _f64(u_old)
+        u_new = np.empty(self.N)
+        ch = ctypes.c_double()
+        self.lib.orc_eik_sweep(self.h, int(t), _ptr(u_old), _ptr(u_new), ctypes.byref(ch))
+        return u_new, ch.value
+
+    def solve(self, u0, delta=0.0, max_rounds=1000):
+        u = _f64(u0).copy()
+        info = np.zeros(3)
+        self.lib.orc_eik_solve(self.h, _ptr(u), float(delta), int(max_rounds), _ptr(info))
+        return u, dict(sweeps=int(info[0]), change=float(info[1]), converged=bool(info[2]))
+
+
+def eikonal_init(n_cells: int, sources) -> np.ndarray:
+    """u0: 0 at the source cells, +inf elsewhere."""
+    u = np.full(n_cells, np.inf)
+    u[np.asarray(sources, dtype=np.int64)] = 0.0
+    return u
 
 
 def base_corner(dim: int, t: int) -> int:

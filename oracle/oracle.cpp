@@ -29,6 +29,9 @@
 //   SSOR apply (SPD form) ............. Sec. 2 (SSOR = LR then RL), Sec. 5
 //   Krylov drivers .................... standard PCG / right-preconditioned
 //                                      BiCGSTAB (not from the paper)
+//   fast sweeping (eikonal) ........... closing remarks of the paper (the
+//                                      same decomposition for the fast
+//                                      sweeping method); Zhao's Godunov update
 //
 // Pins (tests/test_oracle_*.py): Table 1 iteration counts (1D GS natural and
 // decomposed), closed-form SOR/GS contraction rates on the Poisson model,
@@ -44,6 +47,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <utility>
 #include <vector>
 
@@ -748,6 +752,76 @@ int stationary(Problem& pb, int mode, const double* omega, double rtol, int maxi
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Fast sweeping for the eikonal equation |grad u| = f on a 2D grid of spacing
+// h. The paper's closing remarks name the fast sweeping method as another
+// sequential sweep that its decomposition parallelises (details only in its
+// supplement, which is not available); the local update is the Godunov upwind
+// discretisation of Zhao's fast sweeping method (H.-K. Zhao, Math. Comp. 74,
+// 2005):
+//   a = min(u_W, u_E), b = min(u_S, u_N)        (outside the grid: +inf)
+//   |a - b| >= f h :  u~ = min(a, b) + f h
+//   otherwise      :  u~ = (a + b + sqrt(2 (f h)^2 - (a - b)^2)) / 2
+//   u <- min(u, u~)
+// Sources are cells with u = 0 initially (the min keeps them), all others
+// start at +inf.
+// One decomposed sweep at phase t: every subdomain runs a Gauss-Seidel pass
+// from its start corner, the schedule of the linear sweeps (subdomain_corner);
+// inside the subdomain, cells already visited give their new values and the
+// rest their old ones; cells of other subdomains always give old values (the
+// halo of old values, Sec. 3 "Data structure"). With one subdomain the four
+// consecutive phases are Zhao's four alternating orderings.
+// Stop rule: sweeps run in rounds of four phases; the solve ends after the
+// first round whose largest change |u_new - u_old| over its sweeps is <= delta.
+// ---------------------------------------------------------------------------
+double eik_update(double a, double b, double fh) {
+  const double d = a - b;
+  if (!(std::fabs(d) < fh)) return std::min(a, b) + fh;
+  return (a + b + std::sqrt(2.0 * (fh * fh) - d * d)) * 0.5;
+}
+
+struct Eik {
+  Grid g;
+  Partition P;
+  double h = 0.0;
+  std::vector<double> f;
+};
+
+// One decomposed sweep; returns the largest |u_new - u_old|.
+double eik_sweep(const Eik& E, int64_t t, const double* uo, double* un) {
+  const Grid& g = E.g;
+  const int64_t nx = g.n[0], ny = g.n[1];
+  const double inf = std::numeric_limits<double>::infinity();
+  std::copy(uo, uo + g.N, un);
+  for (int iy = 0; iy < E.P.p[1]; ++iy)
+    for (int ix = 0; ix < E.P.p[0]; ++ix) {
+      const int idx[3] = {ix, iy, 0};
+      const int c = subdomain_corner(2, t, idx);
+      const int64_t x0 = E.P.lo[0][ix], x1 = E.P.lo[0][ix + 1];
+      const int64_t y0 = E.P.lo[1][iy], y1 = E.P.lo[1][iy + 1];
+      // value of cell (x, y) as seen from this subdomain's pass
+      auto val = [&](int64_t x, int64_t y) -> double {
+        if (x < 0 || x >= nx || y < 0 || y >= ny) return inf;
+        const bool mine = x >= x0 && x < x1 && y >= y0 && y < y1;
+        return mine ? un[y * nx + x] : uo[y * nx + x];
+      };
+      for (int64_t yy = 0; yy < y1 - y0; ++yy) {
+        const int64_t y = (c & 2) ? y1 - 1 - yy : y0 + yy;
+        for (int64_t xx = 0; xx < x1 - x0; ++xx) {
+          const int64_t x = (c & 1) ? x1 - 1 - xx : x0 + xx;
+          const int64_t i = y * nx + x;
+          const double a = std::min(val(x - 1, y), val(x + 1, y));
+          const double b = std::min(val(x, y - 1), val(x, y + 1));
+          un[i] = std::min(un[i], eik_update(a, b, E.f[i] * E.h));
+        }
+      }
+    }
+  double m = 0.0;
+  for (int64_t i = 0; i < g.N; ++i)
+    if (un[i] != uo[i]) m = std::max(m, uo[i] - un[i]);  // values only decrease
+  return m;
+}
+
+// ---------------------------------------------------------------------------
 // C interface (loaded with ctypes by the tests). Return 0 on success.
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -822,6 +896,51 @@ int orc_ssor_apply(void* h, int mode, double omega, const double* r, double* z) 
 }
 
 int orc_fwd_phase(int d) { return (int)fwd_phase(d); }
+
+void* orc_eik_create(const int64_t* n, double h, const double* f, const int* sub) {
+  Eik* E = new Eik();
+  const int64_t n3[3] = {n[0], n[1], 1};
+  const int sub3[3] = {sub[0], sub[1], 1};
+  if (!(h > 0.0) || !make_grid(E->g, 2, n3, 5) || !make_partition(E->g, sub3, E->P)) {
+    delete E;
+    return nullptr;
+  }
+  E->h = h;
+  E->f.assign(f, f + E->g.N);
+  return E;
+}
+
+void orc_eik_destroy(void* e) { delete static_cast<Eik*>(e); }
+
+// one sweep at phase t; *change = largest |u_new - u_old|
+int orc_eik_sweep(void* e, int64_t t, const double* uo, double* un, double* change) {
+  *change = eik_sweep(*static_cast<Eik*>(e), t, uo, un);
+  return 0;
+}
+
+// rounds of four sweeps (phases 0, 1, 2, 3, 4, ...) from u until a round's
+// largest change is <= delta; u receives the result; info = {sweeps, last
+// round's largest change, converged}
+int orc_eik_solve(void* e, double* u, double delta, int max_rounds, double* info) {
+  Eik& E = *static_cast<Eik*>(e);
+  std::vector<double> a(u, u + E.g.N), b(E.g.N);
+  int64_t t = 0;
+  double m = 0.0;
+  bool done = false;
+  for (int r = 0; r < max_rounds && !done; ++r) {
+    m = 0.0;
+    for (int k = 0; k < 4; ++k, ++t) {
+      m = std::max(m, eik_sweep(E, t, a.data(), b.data()));
+      a.swap(b);
+    }
+    done = m <= delta;
+  }
+  std::copy(a.begin(), a.end(), u);
+  info[0] = (double)t;
+  info[1] = m;
+  info[2] = done ? 1.0 : 0.0;
+  return 0;
+}
 
 int orc_solve(void* h, int method, int prec, int mode, const double* omega, double rtol,
               int maxit, const double* b, double* x, double* info) {
