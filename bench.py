@@ -178,7 +178,8 @@ def main():
     ap.add_argument("--kernel-only", type=int, default=0, metavar="K",
                     help="only factor and run K ILU(0) applies of the workload (for kernel profiling)")
     ap.add_argument("--workload", default="varcoef2048",
-                    choices=["varcoef2048", "poisson64", "poisson3d", "batch512", "serving", "mg2048"],
+                    choices=["varcoef2048", "poisson64", "poisson3d", "batch512", "serving", "mg2048",
+                             "eikonal2048"],
                     help="varcoef2048 is the benchmark; the others print one measurement line each")
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--n3d", type=int, default=256, help="side of the 3D Poisson workload (subdomains of 32^3)")
@@ -593,8 +594,56 @@ def workload_mg2048(args):
                       "bicgstab_ilu0": {k: ilu[k] for k in ("iters", "relres", "wall_s")}}))
 
 
+def workload_eikonal2048(args):
+    """Fast sweeping for |grad u| = f on 2048^2 cells (h = 1/2048, smoothed
+    lognormal slowness, 4 point sources), 16 x 16 subdomains: whole solves to a
+    round of four sweeps with no change (device vector; and from a host vector,
+    copies included), and the time of one sweep with CUDA events around 20."""
+    import numpy as np
+    torch, nd, W = _setup()
+    p = W.eikonal_problem()
+    n = p["n"][0]
+    e = nd.Eikonal(p["n"], p["h"], p["f"], p["sub"])
+    a = torch.tensor(p["u0"], device="cuda")
+    b = torch.empty_like(a)
+    for t in range(4):
+        e.sweep(t, a, b, wait=False)
+        a, b = b, a
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for t in range(20):
+        e.sweep(t, a, b, wait=False)
+        a, b = b, a
+    e1.record()
+    torch.cuda.synchronize()
+    sweep_ms = e0.elapsed_time(e1) / 20
+    walls, host_walls = [], []
+    for k in range(args.warmup + max(1, args.steps)):
+        u = torch.tensor(p["u0"], device="cuda")
+        torch.cuda.synchronize()
+        info = e.solve(u)
+        uh = p["u0"].copy()
+        hinfo = e.solve(uh)
+        if k >= args.warmup:
+            walls.append(info["seconds"])
+            host_walls.append(hinfo["seconds"])
+    e.close()
+    N = n * n
+    peak, kind = measured_peaks()
+    gbs = 24.0 * N / (sweep_ms / 1e3) / 1e9  # u_old and f read, u_new written, 8 B each
+    print(json.dumps({"workload": f"eikonal2d-{n}x{n}-fast-sweeping-fp64-16x16", "metric":
+                      "solve seconds (rounds of 4 sweeps until one changes nothing)",
+                      "sweeps": info["sweeps"], "wall_s": float(np.median(walls)),
+                      "e2e_host_wall_s": float(np.median(host_walls)), "sweep_ms": sweep_ms,
+                      "gcell_updates_per_s": N / (sweep_ms / 1e3) / 1e9,
+                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                                   "peak_kind": kind, "kernel": "eik_sweep_kernel (fp64 pipe bound, see profile)"}}))
+
+
 EXTRA = {"poisson64": workload_poisson64, "poisson3d": workload_poisson3d,
-         "batch512": workload_batch512, "serving": workload_serving, "mg2048": workload_mg2048}
+         "batch512": workload_batch512, "serving": workload_serving, "mg2048": workload_mg2048,
+         "eikonal2048": workload_eikonal2048}
 
 
 if __name__ == "__main__":

@@ -158,6 +158,58 @@ ndiag_status mg_apply(ndiag* h, double omega, const double* r, double* z);
 int ndiag_mg_levels(const ndiag* h);
 
 /*
+ * Fast sweeping for the eikonal equation |grad u| = f on an nx x ny grid of
+ * spacing h, decomposed like the linear sweeps (the paper's closing remarks
+ * apply its decomposition to the fast sweeping method). One sweep at phase t:
+ * every subdomain runs a Gauss-Seidel pass from its start corner (the same
+ * schedule as sor_sweep), with the Godunov update of Zhao's fast sweeping
+ * method (Math. Comp. 74, 2005):
+ *     a = min(u_W, u_E), b = min(u_S, u_N)          (outside the grid: +inf)
+ *     |a - b| >= f h :  u~ = min(a, b) + f h
+ *     otherwise      :  u~ = (a + b + sqrt(2 (f h)^2 - (a - b)^2)) / 2
+ *     u <- min(u, u~)
+ * Inside a subdomain visited cells give new values and the others old ones;
+ * cells of other subdomains give old values. Sources are cells with u = 0 at
+ * the start; every other cell starts at +inf (or any upper bound).
+ */
+typedef struct ndiag_eik ndiag_eik;
+typedef struct {
+  int sweeps;       /* sweeps run (a multiple of 4) */
+  int converged;    /* 1 if the last round's largest change was <= delta */
+  double change;    /* largest |u_new - u_old| over the last round's sweeps */
+  double seconds;   /* wall time of the call */
+  int64_t launches; /* kernels launched on this handle so far */
+} ndiag_eik_info;
+
+/*
+ * eikonal_create -- copy the slowness f (HOST, nx*ny doubles, x fastest,
+ * finite and >= 0) to the device and split the grid into sub[0] x sub[1]
+ * nearly equal subdomains (as ndiag_create). A subdomain and its one-cell halo
+ * must fit in 200 KB (fp64), e.g. up to 158 x 158 cells.
+ * Errors: NDIAG_EINVAL (sizes, h <= 0, f, subdomains too large), NDIAG_ENOMEM.
+ */
+ndiag_status eikonal_create(ndiag_eik** out, const int64_t n[2], double h, const double* f, const int sub[2],
+                            void* cuda_stream);
+void eikonal_destroy(ndiag_eik* e);
+
+/*
+ * eikonal_sweep -- one decomposed sweep at phase t. u_old and u_new are DEVICE
+ * vectors of nx*ny doubles and must differ. If change is not NULL the call
+ * waits and stores the largest |u_new - u_old|; otherwise it is asynchronous.
+ */
+ndiag_status eikonal_sweep(ndiag_eik* e, int64_t t, const double* u_old, double* u_new, double* change);
+
+/*
+ * eikonal_solve -- sweeps at phases 0, 1, 2, ... in rounds of four (one pass
+ * from each start corner per subdomain) until a round's largest change is
+ * <= delta, or max_rounds rounds. u (DEVICE or HOST, detected) holds the start
+ * values on entry and the result on return. The handle keeps two device
+ * vectors for the rounds. Errors: NDIAG_EINVAL, NDIAG_ENOMEM, NDIAG_ENOCONV
+ * (max_rounds reached; u holds the last iterate).
+ */
+ndiag_status eikonal_solve(ndiag_eik* e, double* u, double delta, int max_rounds, ndiag_eik_info* info);
+
+/*
  * ilu0_factor -- ILU(0) (Sec. 5: one symmetric Gauss-Seidel pass on an
  * n-diagonal matrix is ILU(0)). DECOMPOSED: M = (D~ + L_J) D~^-1 (D~ + U_J),
  * L_J / U_J = implicit entries of the forward phase / of its reverse, and

@@ -31,7 +31,7 @@ EXPORTED = ["ndiag_set_allocator", "ndiag_last_error", "ndiag_create", "ndiag_de
             "ndiag_batch_create", "ndiag_batch_autotune", "ndiag_batch_tiles", "ndiag_batch_solve",
             "ndiag_batch_cells", "ndiag_batch_launches", "ndiag_batch_destroy",
             "ndiag_server_create", "serve_submit", "serve_poll", "ndiag_server_wait", "ndiag_server_stats",
-            "ndiag_server_destroy"]
+            "ndiag_server_destroy", "eikonal_create", "eikonal_destroy", "eikonal_sweep", "eikonal_solve"]
 NOALLOC_MAX_CELLS = 1 << 20
 
 
@@ -62,6 +62,11 @@ class Result(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int), ("running", ctypes.c_int), ("max_running", ctypes.c_int),
                 ("solved", ctypes.c_int64), ("budget_bytes", ctypes.c_int64), ("in_use_bytes", ctypes.c_int64)]
+
+
+class EikInfo(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("converged", ctypes.c_int), ("change", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("launches", ctypes.c_int64)]
 
 
 class Counters(ctypes.Structure):
@@ -122,6 +127,11 @@ def load(path: str = LIB_PATH):
     L.ndiag_server_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
     L.ndiag_server_destroy.argtypes = [P]
     L.ndiag_server_destroy.restype = None
+    L.eikonal_create.argtypes = [ctypes.POINTER(P), P, D, P, P, P]
+    L.eikonal_destroy.argtypes = [P]
+    L.eikonal_destroy.restype = None
+    L.eikonal_sweep.argtypes = [P, L64, P, P, P]
+    L.eikonal_solve.argtypes = [P, P, D, I, ctypes.POINTER(EikInfo)]
     if path == LIB_PATH:
         _lib = L
     return L
@@ -393,3 +403,50 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class Eikonal:
+    """Decomposed fast sweeping for |grad u| = f on an nx x ny grid of spacing
+    h, resident on the current CUDA device (fp64)."""
+
+    def __init__(self, n, h, f, sub=(1, 1), stream=None):
+        import torch
+        self.L = load()
+        _install_torch_allocator(self.L)
+        self.n = (int(n[0]), int(n[1]))
+        self.N = self.n[0] * self.n[1]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        fa = np.ascontiguousarray(f, dtype=np.float64).reshape(self.N)
+        n64 = np.array(self.n, dtype=np.int64)
+        sub32 = np.array(list(sub)[:2], dtype=np.int32)
+        h_ = ctypes.c_void_p()
+        _check(self.L, self.L.eikonal_create(ctypes.byref(h_), _ptr(n64), float(h), _ptr(fa), _ptr(sub32),
+                                             ctypes.c_void_p(self.stream.cuda_stream)))
+        self.h = h_
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.eikonal_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, t, u_old, u_new, wait=True):
+        """One sweep at phase t (device tensors); returns the largest change if wait."""
+        ch = ctypes.c_double()
+        _check(self.L, self.L.eikonal_sweep(self.h, int(t), _ptr(u_old), _ptr(u_new),
+                                            ctypes.byref(ch) if wait else None))
+        return ch.value if wait else None
+
+    def solve(self, u, delta=0.0, max_rounds=1000, raise_on_noconv=True):
+        """u: fp64 device tensor or host array, start values in, result out."""
+        info = EikInfo()
+        st = self.L.eikonal_solve(self.h, _ptr(u), float(delta), int(max_rounds), ctypes.byref(info))
+        if st != OK and (raise_on_noconv or st != ENOCONV):
+            _check(self.L, st)
+        return dict(sweeps=info.sweeps, converged=bool(info.converged), change=info.change,
+                    seconds=info.seconds, launches=info.launches, status=STATUS_NAMES[st])

@@ -193,6 +193,18 @@ def poisson3d_problem(n: int = 256, sub: int = 8, seed: int = 1003):
                 b=uniform_rhs(n ** 3, seed), sub=(sub, sub, sub))
 
 
+def eikonal_problem(n: int = 2048, sub: int = 16, seed: int = 1006, sources: int = 4):
+    """Travel times on an n x n grid of the unit square (h = 1/n) through a
+    heterogeneous medium: slowness f = box5x5(exp(N(0, 1))) per cell, `sources`
+    point sources at seeded random cells (u = 0 there, +inf elsewhere)."""
+    g = rng(seed)
+    f = box_filter(np.exp(g.standard_normal((n, n))), 5).ravel()
+    src = np.unique(g.integers(0, n * n, size=sources))
+    u0 = np.full(n * n, np.inf)
+    u0[src] = 0.0
+    return dict(n=(n, n), h=1.0 / n, f=f, u0=u0, sources=src, sub=(sub, sub))
+
+
 def batched_problems(count: int = 512, lo: int = 32, hi: int = 512, seed: int = 1004):
     """count independent variable-coefficient 5-point problems, sides uniform
     in [lo, hi] independently, alpha log-uniform in [1, 100] per cell."""
