@@ -184,8 +184,8 @@ typedef struct {
 /*
  * eikonal_create -- copy the slowness f (HOST, nx*ny doubles, x fastest,
  * finite and >= 0) to the device and split the grid into sub[0] x sub[1]
- * nearly equal subdomains (as ndiag_create). A subdomain and its one-cell halo
- * must fit in 200 KB (fp64), e.g. up to 158 x 158 cells.
+ * nearly equal subdomains (as ndiag_create). A subdomain may have at most 256
+ * rows and 25600 columns (one thread per row).
  * Errors: NDIAG_EINVAL (sizes, h <= 0, f, subdomains too large), NDIAG_ENOMEM.
  */
 ndiag_status eikonal_create(ndiag_eik** out, const int64_t n[2], double h, const double* f, const int sub[2],

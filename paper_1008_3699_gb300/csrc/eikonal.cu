@@ -13,12 +13,14 @@
 // cells of other subdomains give old values (the halo of old values of the
 // paper's data structure, Sec. 3).
 //
-// One CTA per subdomain, one thread per row of it. The subdomain and a
-// one-cell halo are staged in shared memory in the frame of the start corner;
-// the pass is a wavefront over the anti-diagonals of that frame (a cell's two
-// upstream neighbours lie on the previous diagonal), with one barrier per
-// diagonal. Each thread keeps the slowness of the next EK cells of its row in
-// flight, so the global loads stay off the wavefront's critical path. Every operation is
+// One CTA per subdomain, one thread per row of it, in the frame of the start
+// corner. The pass is a wavefront over the anti-diagonals of that frame: at
+// diagonal d the thread of row ly updates cell d - ly. Its upstream
+// neighbours are its own previous value (left) and the value the thread below
+// made at d - 1 (down: a lane shuffle, across warps a shared word, one barrier
+// per diagonal); its downstream neighbours and the slowness are old values
+// streamed along the row with EK loads in flight. Nothing of the subdomain is
+// staged, so many CTAs share an SM. Every operation is
 // rounded on its own (no contraction), so a sweep reproduces the plain
 // row-by-row pass exactly. The largest change of a sweep goes to a device word
 // (atomicMax on the bits of a non-negative double).
@@ -32,14 +34,13 @@
 namespace nd {
 namespace {
 
-constexpr int EMAX = 1024;  // threads per CTA at most: one per row of the tallest subdomain
-constexpr int EK = 8;       // slowness values in flight per thread
+constexpr int EMAX = 256;  // threads per CTA at most: one per row of the tallest subdomain
+constexpr int EK = 4;      // values of each stream in flight per thread
 
 struct EikP {
   int nx, ny;
   Split sx, sy;
   int base;   // start corner of subdomain (0, 0) at this phase
-  int tw;     // row length of the shared tile (largest subdomain width + 2)
   double h;
   const double* f;
   const double* uo;
@@ -55,35 +56,51 @@ __device__ __forceinline__ double godunov(double a, double b, double fh) {
 }
 
 __global__ void __launch_bounds__(EMAX) eik_sweep_kernel(EikP P) {
-  extern __shared__ double tile[];
+  extern __shared__ double hrow[];           // old values of the frame row below row 0
+  __shared__ double xfer[2][EMAX / 32];      // last lane's new value, per warp and diagonal parity
   const int ix = blockIdx.x % P.sx.p, iy = blockIdx.x / P.sx.p;
   const int c = P.base ^ (ix & 1) ^ ((iy & 1) << 1);
   const int x0 = P.sx.lo(ix), w = P.sx.len(ix);
   const int y0 = P.sy.lo(iy), hh = P.sy.len(iy);
-  const int tw = P.tw, nt = blockDim.x;
   const double inf = __longlong_as_double(0x7ff0000000000000LL);
-  // frame coordinate -> grid coordinate (lx in -1..w, ly in -1..hh)
+  // frame coordinate -> grid coordinate
   auto gx = [&](int lx) { return (c & 1) ? x0 + w - 1 - lx : x0 + lx; };
   auto gy = [&](int ly) { return (c & 2) ? y0 + hh - 1 - ly : y0 + ly; };
-  // stage the subdomain and its halo (old values; +inf outside the grid)
-  const int tn = (w + 2) * (hh + 2);
-  for (int k = threadIdx.x; k < tn; k += nt) {
-    const int lx = k % (w + 2) - 1, ly = k / (w + 2) - 1;
-    const int X = gx(lx), Y = gy(ly);
-    const bool in = X >= 0 && X < P.nx && Y >= 0 && Y < P.ny;
-    tile[(ly + 1) * tw + lx + 1] = in ? __ldcg(P.uo + (int64_t)Y * P.nx + X) : inf;
-  }
-  // thread ly owns frame row ly and meets its cell lx = d - ly at diagonal d;
-  // the slowness of its next EK cells is in flight in fr[] (slot (lx + EK) % EK)
-  const int ly = threadIdx.x;
+  const int ly = threadIdx.x, lane = ly & 31, wid = ly >> 5;
   const bool row = ly < hh;
-  const double* frow = P.f + (int64_t)(row ? gy(ly) : y0) * P.nx;
-  auto fload = [&](int lx) -> double { return row && lx >= 0 && lx < w ? __ldg(frow + gx(lx)) : 0.0; };
-  double fr[EK];
+  {
+    const int Yb = gy(-1);
+    const bool ok = Yb >= 0 && Yb < P.ny;
+    for (int lx = threadIdx.x; lx < w; lx += blockDim.x)
+      hrow[lx] = ok ? __ldcg(P.uo + (int64_t)Yb * P.nx + gx(lx)) : inf;
+  }
+  // the three streams of this thread's row: old u of the row (frame lx -1..w),
+  // old u of the row above (lx 0..w-1) and the slowness (lx 0..w-1)
+  const int Yr = gy(row ? ly : 0), Yu = gy(ly + 1);
+  const bool up_ok = row && Yu >= 0 && Yu < P.ny;
+  const double* urow = P.uo + (int64_t)Yr * P.nx;
+  const double* uup = P.uo + (int64_t)(up_ok ? Yu : Yr) * P.nx;
+  const double* frow = P.f + (int64_t)Yr * P.nx;
+  auto ld_r = [&](int lx) -> double {
+    const int X = gx(lx);
+    return row && lx >= -1 && lx <= w && X >= 0 && X < P.nx ? __ldcg(urow + X) : inf;
+  };
+  auto ld_u = [&](int lx) -> double { return up_ok && lx >= 0 && lx < w ? __ldcg(uup + gx(lx)) : inf; };
+  auto ld_f = [&](int lx) -> double { return row && lx >= 0 && lx < w ? __ldg(frow + gx(lx)) : 0.0; };
+  // slot j of a ring serves the diagonals d = j (mod EK); at diagonal d the
+  // thread's cell is lx = d - ly and it needs r(lx + 1), up(lx), f(lx)
+  double rr[EK], ru[EK], rf[EK];
 #pragma unroll
-  for (int j = 0; j < EK; ++j) fr[j] = fload(j - ly);
-  __syncthreads();
+  for (int j = 0; j < EK; ++j) {
+    rr[j] = ld_r(j - ly + 1);
+    ru[j] = ld_u(j - ly);
+    rf[j] = ld_f(j - ly);
+  }
+  double left = ld_r(-1);   // new value of the cell to the left (the halo at first)
+  double cur = ld_r(-ly);   // old value of the thread's cell
+  double v = inf;           // the thread's last new value
   double m = 0.0;
+  __syncthreads();
   const int D = w + hh - 1;
   for (int d0 = 0; d0 < D; d0 += EK) {
 #pragma unroll
@@ -91,31 +108,30 @@ __global__ void __launch_bounds__(EMAX) eik_sweep_kernel(EikP P) {
       const int d = d0 + j;
       if (d < D) {  // the same for the whole block
         const int lx = d - ly;
-        const double fc = fr[j];
-        fr[j] = fload(lx + EK);
+        const double right = rr[j], up = ru[j], fc = rf[j];
+        rr[j] = ld_r(lx + 1 + EK);
+        ru[j] = ld_u(lx + EK);
+        rf[j] = ld_f(lx + EK);
+        // new value of the cell below, made by the thread below at d - 1
+        double down = __shfl_up_sync(0xffffffffu, v, 1);
+        if (lane == 0) down = wid == 0 ? (lx >= 0 && lx < w ? hrow[lx] : inf) : xfer[(d - 1) & 1][wid - 1];
         if (row && lx >= 0 && lx < w) {
-          double* q = tile + (ly + 1) * tw + lx + 1;
-          const double a = fmin(q[-1], q[1]);
-          const double b = fmin(q[-tw], q[tw]);
-          const double u = q[0];
-          const double v = fmin(u, godunov(a, b, __dmul_rn(fc, P.h)));
-          q[0] = v;
-          if (__double_as_longlong(v) != __double_as_longlong(u)) m = fmax(m, __dsub_rn(u, v));
+          const double a = fmin(left, right);
+          const double b = fmin(down, up);
+          v = fmin(cur, godunov(a, b, __dmul_rn(fc, P.h)));
+          if (__double_as_longlong(v) != __double_as_longlong(cur)) m = fmax(m, __dsub_rn(cur, v));
+          P.un[(int64_t)Yr * P.nx + gx(lx)] = v;
+          left = v;
         }
+        cur = right;
+        if (lane == 31) xfer[d & 1][wid] = v;
         __syncthreads();
       }
     }
   }
-  // write back row by row in grid order
-  for (int k = threadIdx.x; k < w * hh; k += nt) {
-    const int X = x0 + k % w, Y = y0 + k / w;
-    const int lx = (c & 1) ? x0 + w - 1 - X : X - x0;
-    const int lyy = (c & 2) ? y0 + hh - 1 - Y : Y - y0;
-    P.un[(int64_t)Y * P.nx + X] = tile[(lyy + 1) * tw + lx + 1];
-  }
   // largest change of the CTA
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(P.change, (unsigned long long)__double_as_longlong(m));
+  if (lane == 0 && m > 0.0) atomicMax(P.change, (unsigned long long)__double_as_longlong(m));
 }
 
 bool device_ptr(const void* p) {
@@ -142,7 +158,7 @@ struct ndiag_eik {
   size_t buf_bytes = 0;
   unsigned long long* change = nullptr;
   unsigned long long* change_host = nullptr;
-  int tw = 0, threads = 0;
+  int threads = 0;
   size_t smem = 0;
   int64_t launches = 0;
 };
@@ -156,7 +172,6 @@ ndiag_status eik_launch(ndiag_eik* e, int64_t t, const double* uo, double* un) {
   P.sx = e->sx;
   P.sy = e->sy;
   P.base = base_corner(2, t);
-  P.tw = e->tw;
   P.h = e->h;
   P.f = e->f;
   P.uo = uo;
@@ -203,16 +218,14 @@ ndiag_status eikonal_create(ndiag_eik** out, const int64_t n[2], double h, const
   e->h = h;
   e->stream = (cudaStream_t)cuda_stream;
   const int wmax = e->sx.q + (e->sx.r ? 1 : 0), hmax = e->sy.q + (e->sy.r ? 1 : 0);
-  e->tw = wmax + 2;
-  e->smem = sizeof(double) * (size_t)(wmax + 2) * (size_t)(hmax + 2);
+  e->smem = sizeof(double) * (size_t)wmax;
   e->threads = 32 * ((hmax + 31) / 32);
   if (e->smem > 200 * 1024 || hmax > EMAX) {
     delete e;
-    set_error("eikonal_create: a subdomain and its halo must fit in 200 KB of shared memory, "
-              "and a subdomain may have at most 1024 rows");
+    set_error("eikonal_create: a subdomain may have at most 256 rows and 25600 columns");
     return NDIAG_EINVAL;
   }
-  // the same ceiling for every handle, so that handles of different tile sizes coexist
+  // the same ceiling for every handle, so that handles of different widths coexist
   if (cudaFuncSetAttribute(eik_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
       cudaSuccess) {
     cudaGetLastError();

@@ -34,7 +34,8 @@ CASES = [
     ((131, 97), (3, 4), 2),     # ragged parts
     ((200, 150), (4, 3), 3),
     ((40, 300), (1, 3), 4),     # tall strips
-    ((256, 256), (2, 2), 5),    # 128 x 128 tiles, as in the 2048^2 workload
+    ((256, 256), (2, 2), 5),    # 128 x 128 subdomains, as in the 2048^2 workload
+    ((70, 600), (1, 3), 8),     # 200 rows: seven warps per subdomain
     ((97, 1), (5, 1), 6),       # one row
 ]
 
@@ -116,7 +117,7 @@ def test_refused_arguments(nd):
     with pytest.raises(nd.NdiagError):
         nd.Eikonal((16, 16), 1.0, np.ones(256), (17, 1))
     with pytest.raises(nd.NdiagError):
-        nd.Eikonal((400, 400), 1.0, np.ones(160000), (1, 1))  # tile beyond 200 KB
+        nd.Eikonal((40, 400), 1.0, np.ones(16000), (1, 1))  # more than 256 rows
     e = nd.Eikonal((16, 16), 1.0, np.ones(256), (2, 2))
     a = torch.zeros(256, dtype=torch.float64, device="cuda")
     with pytest.raises(nd.NdiagError):
