@@ -213,8 +213,12 @@ ndiag_status eikonal_solve(ndiag_eik* e, double* u, double delta, int max_rounds
  * ilu0_factor -- ILU(0) (Sec. 5: one symmetric Gauss-Seidel pass on an
  * n-diagonal matrix is ILU(0)). DECOMPOSED: M = (D~ + L_J) D~^-1 (D~ + U_J),
  * L_J / U_J = implicit entries of the forward phase / of its reverse, and
- * d~_i = a_ii - sum_{j in J_i, i not in J_j} a_ij a_ji / d~_j. NATURAL: the
- * same with one lexicographic subdomain (5/7-point).
+ * d~_i = a_ii - sum_{j in J_i, i not in J_j} a_ij a_ji / d~_j (for the 9-point
+ * molecule this is D-ILU: the off-diagonals of A are kept). NATURAL: the same
+ * with one lexicographic subdomain for 5/7-point matrices; for 9-point
+ * matrices the true ILU(0) of the lexicographic order, whose off-diagonal
+ * entries are modified too (IKJ elimination on the 9-point pattern, Saad
+ * Alg. 10.4), applied as (D + L') D^-1 (D + U') with D = diag(U).
  * Errors: NDIAG_EBREAKDOWN on a zero pivot (reported at the next sync).
  */
 ndiag_status ilu0_factor(ndiag* h, int mode);

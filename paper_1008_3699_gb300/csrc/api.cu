@@ -131,7 +131,9 @@ size_t coef_size(int precision) {
 
 }  // namespace
 
-ndiag_status build_scaled(Handle* h, ScaledSet& set, const double* piv) {
+ndiag_status build_scaled(Handle* h, ScaledSet& set, const double* piv) { return build_scaled_from(h, set, h->A64, piv); }
+
+ndiag_status build_scaled_from(Handle* h, ScaledSet& set, const double* A, const double* piv) {
   const size_t bytes = coef_size(h->precision) * (size_t)h->stencil * (size_t)h->N;
   if (!set.base) {
     set.base = dev_alloc(bytes, h->stream);
@@ -143,13 +145,13 @@ ndiag_status build_scaled(Handle* h, ScaledSet& set, const double* piv) {
   ++set.version;
   switch (h->precision) {
     case NDIAG_FP64:
-      scaled_set_kernel<double><<<grid, 256, 0, h->stream>>>(h->N, h->stencil, h->A64, piv, (double*)set.base);
+      scaled_set_kernel<double><<<grid, 256, 0, h->stream>>>(h->N, h->stencil, A, piv, (double*)set.base);
       break;
     case NDIAG_FP32:
-      scaled_set_kernel<float><<<grid, 256, 0, h->stream>>>(h->N, h->stencil, h->A64, piv, (float*)set.base);
+      scaled_set_kernel<float><<<grid, 256, 0, h->stream>>>(h->N, h->stencil, A, piv, (float*)set.base);
       break;
     default:
-      scaled_set_kernel<__half><<<grid, 256, 0, h->stream>>>(h->N, h->stencil, h->A64, piv, (__half*)set.base);
+      scaled_set_kernel<__half><<<grid, 256, 0, h->stream>>>(h->N, h->stencil, A, piv, (__half*)set.base);
   }
   ND_CUDA(cudaGetLastError());
   return NDIAG_OK;
@@ -431,13 +433,20 @@ ndiag_status sor_sweep(ndiag* h, int mode, const double* omega, int64_t t, const
 
 ndiag_status ilu0_factor(ndiag* h, int mode) {
   if (!h || (mode != NDIAG_NATURAL && mode != NDIAG_DECOMPOSED)) return NDIAG_EINVAL;
+  if (h->stencil == 9 && mode == NDIAG_NATURAL) {
+    // true ILU(0) with modified off-diagonals, as a 9 x N matrix (D + L') D^-1 (D + U')
+    const size_t fb = sizeof(double) * 9 * (size_t)h->N;
+    double* F = (double*)dev_alloc(fb, h->stream);
+    if (!F) return NDIAG_ENOMEM;
+    ndiag_status st = launch_ilu_factor9_natural(h, F);
+    if (st == NDIAG_OK) st = build_scaled_from(h, h->ilu, F, F);
+    dev_free(F, fb, h->stream);
+    if (st == NDIAG_OK) st = check_status(h);
+    h->ilu_mode = st == NDIAG_OK ? mode : -1;
+    return st;
+  }
   double* dt = (double*)dev_alloc(sizeof(double) * (size_t)h->N, h->stream);
   if (!dt) return NDIAG_ENOMEM;
-  if (h->stencil == 9 && mode == NDIAG_NATURAL) {
-    dev_free(dt, sizeof(double) * (size_t)h->N, h->stream);
-    set_error("natural-order ILU(0) of the 9-point stencil is not available (decomposed D-ILU is)");
-    return NDIAG_EINVAL;
-  }
   ndiag_status st = h->dim == 3        ? launch_ilu_factor3d_into(h, mode, dt)
                     : h->stencil == 9 ? launch_ilu_factor9_into(h, mode, dt)
                                       : launch_ilu_factor2d_into(h, mode, dt);

@@ -180,6 +180,10 @@ ndiag_status launch_tri_sweep2d_scratch(Handle* h, int kind, int mode, int64_t t
                                         const void* rhs, void* xnew, unsigned* sync, size_t sync_bytes,
                                         void* twin, size_t twin_bytes);
 ndiag_status build_scaled(Handle* h, ScaledSet& set, const double* piv);
+// the same from another s x N matrix A (entries / piv, 1 / piv)
+ndiag_status build_scaled_from(Handle* h, ScaledSet& set, const double* A, const double* piv);
+// natural-order ILU(0) of a 9-point matrix into F (9 x N, ilu9n.cu)
+ndiag_status launch_ilu_factor9_natural(Handle* h, double* F);
 // One prepared launch of the staged 2D sweep over several handles (a batch of
 // independent problems): device arrays of per-problem parameters and slab
 // offsets, rebuilt by batch_sweep_prepare, launched by batch_sweep_launch

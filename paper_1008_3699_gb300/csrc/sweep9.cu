@@ -386,7 +386,7 @@ template <class T, class TC, int KIND, bool OM1>
 ndiag_status run9(Handle* h, P9<T, TC>& P, unsigned nsub, double bytes) {
   const int w = P.sx.len(0), hh = P.sy.len(0);
   // twin lines, then the pencil path's four-level ring (per subdomain)
-  P.half_elems = w + hh + 1 + 4 * hh;
+  P.half_elems = w + hh + 1 + (hh <= T9 ? 4 * hh : 0);  // no ring where no row-per-thread pencil fits
   // pairing: coupled x-interfaces join ix and ix + 1 where ix has the parity
   // at which a subdomain starts at its max-x side
   P.paired = P.coupled && hh <= T9 / 2 && P.sx.p > 1;

@@ -1,8 +1,10 @@
 """GPU parity of the 2D 9-point path (level sweep with x-interface lockstep,
 sweep9.cu) against the CPU oracle, through the C ABI: SOR sweeps of every
 phase and the natural ordering, the decomposed D-ILU factor and apply to 1e-12
-(fp64), fp32 sweeps to 2e-5, and an ILU(0)-BiCGSTAB solve of the 9-point
-convection-diffusion operator inside the oracle's iteration envelope.
+(fp64), fp32 sweeps to 2e-5, an ILU(0)-BiCGSTAB solve of the 9-point
+convection-diffusion operator inside the oracle's iteration envelope, and the
+natural-order true ILU(0) (modified off-diagonals): apply to 1e-12 / 2e-5,
+solve count inside the oracle's envelope, zero pivot reported.
 """
 import numpy as np
 import pytest
@@ -121,13 +123,68 @@ def test_bicgstab_dilu9_convdiff_in_oracle_envelope(nd):
     h.close()
 
 
-def test_nine_point_ssor_and_natural_ilu_are_refused(nd):
+def test_nine_point_ssor_is_refused(nd):
     n = (12, 10)
     d = _rand9(n, 97)
     h = nd.NDiag(2, n, 9, d, (2, 2), "fp64")
     z = _t(np.zeros(120))
     with pytest.raises(nd.NdiagError):
         h.ssor_apply(1.0, _t(np.ones(120)), z)
+    h.close()
+
+
+@pytest.mark.parametrize("n", [(20, 17), (33, 25), (9, 12), (1, 7), (7, 1), (2, 5), (300, 40)])
+def test_natural_ilu0_apply9_fp64(nd, n):
+    # true ILU(0) (modified off-diagonals) in natural order against the oracle's IKJ factor
+    d = _rand9(n, 98)
+    N = n[0] * n[1]
+    r = np.random.default_rng(99).uniform(-1, 1, N)
+    ref = oracle.Problem(2, n, 9, d, (1, 1))
+    ref.ilu0_factor(oracle.NATURAL)
+    h = nd.NDiag(2, n, 9, d, (2, 1) if n[0] > 1 else (1, 1), "fp64")
+    h.ilu0_factor(nd.NATURAL)
+    z = _t(np.zeros(N))
+    h.ilu0_apply(_t(r), z)
+    assert _rel(z.cpu().numpy(), ref.ilu0_apply(r)) <= 1e-12
+    h.close()
+
+
+def test_natural_ilu0_9_fp32_and_solve(nd):
+    import torch
+    n = 48
+    d = W.convdiff9(n, 7.0, 0.6)
+    N = n * n
+    b = W.uniform_rhs(N, 1007)
+    ref = oracle.Problem(2, (n, n), 9, d, (1, 1))
+    ref.ilu0_factor(oracle.NATURAL)
+    h32 = nd.NDiag(2, (n, n), 9, d, (1, 1), "fp32")
+    h32.ilu0_factor(nd.NATURAL)
+    z = _t(np.zeros(N), torch.float32)
+    h32.ilu0_apply(_t(b, torch.float32), z)
+    assert _rel(z.cpu().numpy(), ref.ilu0_apply(b)) <= 2e-5
+    h32.close()
+    counts = []
+    g = np.random.default_rng(4321)
+    for j in range(7):
+        bb = b if j == 0 else b * (1.0 + 1e-15 * g.standard_normal(N))
+        _, info = ref.solve(oracle.BICGSTAB, oracle.PREC_ILU0, oracle.NATURAL, 1.0, 1e-8, 5000, bb)
+        counts.append(info["iters"])
+    h = nd.NDiag(2, (n, n), 9, d, (3, 3), "fp64")
+    h.ilu0_factor(nd.NATURAL)
+    x = _t(np.zeros(N))
+    info = h.solve(nd.BICGSTAB, nd.PREC_ILU0, _t(b), x, rtol=1e-8, maxit=5000, mode=nd.NATURAL)
+    assert info["relres"] <= 1e-8
+    assert min(counts) - 1 <= info["iters"] <= max(counts) + 1, (info, counts)
+    h.close()
+
+
+def test_natural_ilu0_9_zero_pivot_is_reported(nd):
+    # a row whose elimination cancels its pivot: A = [[1, 1], [1, 1]] on a 2 x 1 grid
+    d = np.zeros((9, 2))
+    d[0] = 1.0
+    d[2, 0] = 1.0   # E of cell 0
+    d[1, 1] = 1.0   # W of cell 1
+    h = nd.NDiag(2, (2, 1), 9, d, (1, 1), "fp64")
     with pytest.raises(nd.NdiagError):
         h.ilu0_factor(nd.NATURAL)
     h.close()
