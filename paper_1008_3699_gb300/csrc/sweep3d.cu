@@ -341,8 +341,15 @@ __global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
   const int tcode = S.t[0] | (S.t[1] << 1) | (S.t[2] << 2);
   const bool blocks_only = P.region != REG_ALL && P.region != REG_INTERIOR;
   const int umax = max(w, max(h, d));
-  for (int it = 0; it <= lmax; ++it) {
-    const int L = P.transposed ? lmax - it : it;
+  // block cells lie on start faces: a face cell (two free coordinates) is on
+  // a level <= 2 (umax - 1), an edge cell (one) on a level <= umax - 1, the
+  // corner on level 0; the passes over blocks skip the empty levels above
+  const int lreg = P.region == REG_CORNERS ? 0
+                   : P.region == REG_EDGES ? min(lmax, umax - 1)
+                   : blocks_only           ? min(lmax, 2 * (umax - 1))
+                                           : lmax;
+  for (int it = 0; it <= lreg; ++it) {
+    const int L = P.transposed ? lreg - it : it;
     // REG_ALL / REG_INTERIOR: every row (y, z) meets its cell x = L - y - z.
     // Block regions: only cells with a zero coordinate can be blocks; cell c
     // of a level enumerates face a = c / umax (coordinate a = 0), the cell
