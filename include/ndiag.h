@@ -158,6 +158,16 @@ ndiag_status mg_apply(ndiag* h, double omega, const double* r, double* z);
 int ndiag_mg_levels(const ndiag* h);
 
 /*
+ * ndiag_selftest_wait -- exercises the failure path of the bounded
+ * device-side waits that the sweeps use between CTAs: one warp waits on a
+ * device word that nothing sets, gives up after the bound (about 2 s of GPU
+ * clock), records the timeout and returns. Returns NDIAG_ETIMEOUT when the
+ * path works (the status word is cleared again and the handle stays usable);
+ * NDIAG_OK would mean the wait did not run out.
+ */
+ndiag_status ndiag_selftest_wait(ndiag* h);
+
+/*
  * Fast sweeping for the eikonal equation |grad u| = f on an nx x ny grid of
  * spacing h, decomposed like the linear sweeps (the paper's closing remarks
  * apply its decomposition to the fast sweeping method). One sweep at phase t:

@@ -26,7 +26,7 @@ PREC_NONE, PREC_SSOR, PREC_ILU0, PREC_MG = 0, 1, 2, 3
 
 # every symbol include/ndiag.h declares
 EXPORTED = ["ndiag_set_allocator", "ndiag_last_error", "ndiag_create", "ndiag_destroy", "ndiag_cells",
-            "ndiag_precision", "sor_sweep", "ssor_apply", "mg_apply", "ndiag_mg_levels", "ilu0_factor", "ilu0_apply", "ndiag_residual",
+            "ndiag_precision", "sor_sweep", "ssor_apply", "mg_apply", "ndiag_mg_levels", "ndiag_selftest_wait", "ilu0_factor", "ilu0_apply", "ndiag_residual",
             "krylov_solve", "ndiag_tune_omega", "ndiag_profile", "ndiag_read_counters", "ilu0_apply_noalloc",
             "ndiag_batch_create", "ndiag_batch_autotune", "ndiag_batch_tiles", "ndiag_batch_solve",
             "ndiag_batch_cells", "ndiag_batch_launches", "ndiag_batch_destroy",
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
     L.ssor_apply.argtypes = [P, I, D, P, P]
     L.mg_apply.argtypes = [P, D, P, P]
     L.ndiag_mg_levels.argtypes = [P]
+    L.ndiag_selftest_wait.argtypes = [P]
     L.ilu0_factor.argtypes = [P, I]
     L.ilu0_apply.argtypes = [P, P, P]
     L.ilu0_apply_noalloc.argtypes = [P, P, P]
@@ -229,6 +230,10 @@ class NDiag:
 
     def mg_levels(self):
         return int(self.L.ndiag_mg_levels(self.h))
+
+    def selftest_wait(self):
+        """Runs the bounded-wait failure path; returns the status name (ETIMEOUT expected)."""
+        return STATUS_NAMES[self.L.ndiag_selftest_wait(self.h)]
 
     def ilu0_factor(self, mode=DECOMPOSED):
         _check(self.L, self.L.ilu0_factor(self.h, mode))
