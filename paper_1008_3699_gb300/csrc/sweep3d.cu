@@ -75,6 +75,16 @@ struct Sub {
 
 // entry index (0-based in c[]) of the neighbour along axis a towards -a / +a
 __device__ __forceinline__ int ent(int a, int plus) { return 2 * a + plus; }
+// the entry array itself; with a known at compile time both candidates are
+// constant indices, so the parameter block need not be copied to local memory
+template <class T, class TC>
+__device__ __forceinline__ const TC* cptr(const GP<T, TC>& P, int a, int plus) {
+  return plus ? P.c[2 * a + 1] : P.c[2 * a];
+}
+// r-th set bit (axis) of a coupled-axis mask, at compile time
+__host__ __device__ constexpr int axis_of(int CM, int r) {
+  return r == 0 ? ((CM & 1) ? 0 : (CM & 2) ? 1 : 2) : axis_of(CM & (CM - 1), r - 1);
+}
 
 template <class T, class TC>
 __device__ __forceinline__ Sub subdomain(const GP<T, TC>& P, unsigned b) {
@@ -150,18 +160,32 @@ __device__ __forceinline__ bool in_region(int region, int C) {
 // One coupled block: the own cell (x, y, z) lies at 0 on the NC coupled axes C.
 // Solves the block, stores the own member to xnew and the twins to the twin
 // store, and returns the own member's value.
-template <class T, class TC, int KIND, bool OM1, int NC>
+// CM = the coupled axes as a compile-time mask (then C == CM), or 0: taken
+// from C at run time. The 4-byte variants use the mask, so that every axis
+// index is a constant and no small array lives in local memory; the fp64
+// variants keep one instantiation per block size, which holds their code
+// and registers down.
+template <class T, class TC, int KIND, bool OM1, int NC, int CM = 0>
 __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const TwinIdx& TI, T* tw, int x, int y,
                                       int z, int C, int tcode) {
   const int own[3] = {x, y, z};
   // canonical member order: bit r of a member index <-> r-th coupled axis,
   // set when the member has the larger global coordinate along it
   int axes[3], nC = 0;
-  for (int a = 0; a < 3; ++a)
-    if (C >> a & 1) axes[nC++] = a;
+  if constexpr (CM != 0) {
+    C = CM;
+    axes[0] = axis_of(CM, 0);
+    axes[1] = NC > 1 ? axis_of(CM, 1) : 0;
+    axes[2] = NC > 2 ? axis_of(CM, 2) : 0;
+    nC = NC;
+  } else {
+    for (int a = 0; a < 3; ++a)
+      if (C >> a & 1) axes[nC++] = a;
+  }
   constexpr int n = 1 << NC;  // nC == NC
   int mo = 0;  // own member
-  for (int r = 0; r < nC; ++r)
+#pragma unroll
+  for (int r = 0; r < NC; ++r)
     if (S.c[axes[r]] == 0) mo |= 1 << r;
   T M[n][n], hv[n];
   int64_t gidx[n];
@@ -171,7 +195,7 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
 #pragma unroll
     for (int r = 0; r < NC; ++r) {
       const int a = axes[r];
-      T g = ldco<T, TC>(P.c[ent(a, cm[a] ? 1 : 0)] + gi);
+      T g = ldco<T, TC>(cptr(P, a, cm[a] ? 1 : 0) + gi);
       if (!OM1) g *= om;
       M[m][m ^ (1 << r)] = g;
     }
@@ -179,7 +203,8 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
 #pragma unroll
   for (int m = 0; m < n; ++m) {
     int lc[3] = {own[0], own[1], own[2]}, sub = 0;
-    for (int r = 0; r < nC; ++r)
+#pragma unroll
+    for (int r = 0; r < NC; ++r)
       if (((m ^ mo) >> r) & 1) {
         lc[axes[r]] = -1;
         sub |= 1 << axes[r];
@@ -206,11 +231,11 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
           const int dn = cm[a] ? 0 : 1;  // downstream side of the member along a
           const int gd = gc[a] + (dn ? 1 : -1);
           if (gd >= 0 && gd < P.n[a])
-            e = fma(-ldco<T, TC>(P.c[ent(a, dn)] + gi), __ldg(P.xold + gi + (dn ? P.stride[a] : -P.stride[a])), e);
+            e = fma(-ldco<T, TC>(cptr(P, a, dn) + gi), __ldg(P.xold + gi + (dn ? P.stride[a] : -P.stride[a])), e);
           const bool implicit_up = (C >> a & 1) || lc[a] >= 1;
           const int gu = gc[a] + (dn ? -1 : 1);
           if (!implicit_up && gu >= 0 && gu < P.n[a])
-            e = fma(-ldco<T, TC>(P.c[ent(a, 1 - dn)] + gi), __ldg(P.xold + gi + (dn ? -P.stride[a] : P.stride[a])), e);
+            e = fma(-ldco<T, TC>(cptr(P, a, 1 - dn) + gi), __ldg(P.xold + gi + (dn ? -P.stride[a] : P.stride[a])), e);
         }
         acc = OM1 ? e : fma(om, e, (T(1) - om) * __ldg(P.xold + gi));
       } else if (KIND == KIND_TRI_SCALED) {
@@ -227,7 +252,7 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
         if (C >> a & 1) {
           // the block partner along a (set by partners)
         } else if (lc[a] >= 1) {
-          T g = ldco<T, TC>(P.c[ent(a, up)] + gi);
+          T g = ldco<T, TC>(cptr(P, a, up) + gi);
           if (!OM1) g *= om;
           const int64_t gp = gi + (up ? P.stride[a] : -P.stride[a]);
           T v;
@@ -262,7 +287,7 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
           inside = lc[a] + 1 < S.len[a];
         }
         if (!inside) continue;
-        T g = ldco<T, TC>(P.c[ent(a, dn)] + gi);
+        T g = ldco<T, TC>(cptr(P, a, dn) + gi);
         if (!OM1) g *= om;
         const int64_t gq = gi + (dn ? P.stride[a] : -P.stride[a]);
         T v;
@@ -311,7 +336,8 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
       P.xnew[gidx[m]] = xs[m];
     } else {
       int lc[3] = {own[0], own[1], own[2]}, sub = 0;
-      for (int r = 0; r < nC; ++r)
+#pragma unroll
+      for (int r = 0; r < NC; ++r)
         if (((m ^ mo) >> r) & 1) {
           lc[axes[r]] = -1;
           sub |= 1 << axes[r];
@@ -319,11 +345,15 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
       tw[TI.slot(sub, lc)] = xs[m];
     }
   }
-  return xs[mo];
+  T own_x = xs[0];
+#pragma unroll
+  for (int m = 1; m < n; ++m)
+    if (m == mo) own_x = xs[m];
+  return own_x;
 }
 
-// the 8x8 corner block (one per subdomain) out of line, so that its registers
-// do not weigh on the face and edge blocks
+// the 8x8 corner block (one per subdomain) of the fp64 variants out of line,
+// so that its registers do not weigh on the face and edge blocks
 template <class T, class TC, int KIND, bool OM1>
 __device__ __noinline__ void corner_block(const GP<T, TC>& P, const Sub& S, const TwinIdx& TI, T* tw, int x, int y,
                                           int z, int C, int tcode) {
@@ -397,10 +427,10 @@ __global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
               const int dn = S.c[a] ? 0 : 1;
               const int gd = gc[a] + (dn ? 1 : -1);
               if (gd >= 0 && gd < P.n[a])
-                e = fma(-ldco<T, TC>(P.c[ent(a, dn)] + gi), __ldg(P.xold + gi + (dn ? P.stride[a] : -P.stride[a])), e);
+                e = fma(-ldco<T, TC>(cptr(P, a, dn) + gi), __ldg(P.xold + gi + (dn ? P.stride[a] : -P.stride[a])), e);
               const int gu = gc[a] + (dn ? -1 : 1);
               if (own[a] == 0 && gu >= 0 && gu < P.n[a])
-                e = fma(-ldco<T, TC>(P.c[ent(a, 1 - dn)] + gi), __ldg(P.xold + gi + (dn ? -P.stride[a] : P.stride[a])), e);
+                e = fma(-ldco<T, TC>(cptr(P, a, 1 - dn) + gi), __ldg(P.xold + gi + (dn ? -P.stride[a] : P.stride[a])), e);
             }
             acc = OM1 ? e : fma(om, e, (T(1) - om) * __ldg(P.xold + gi));
           } else if (KIND == KIND_TRI_SCALED) {
@@ -413,7 +443,7 @@ __global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
           for (int a = 0; a < 3; ++a) {
             if (own[a] < 1) continue;
             const int up = S.c[a] ? 1 : 0;
-            T g = ldco<T, TC>(P.c[ent(a, up)] + gi);
+            T g = ldco<T, TC>(cptr(P, a, up) + gi);
             if (!OM1) g *= om;
             acc = fma(-g, __ldcg(P.xnew + gi + (up ? P.stride[a] : -P.stride[a])), acc);
           }
@@ -423,7 +453,7 @@ __global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
           for (int a = 0; a < 3; ++a) {
             if (own[a] + 1 >= S.len[a]) continue;
             const int dn = S.c[a] ? 0 : 1;
-            T g = ldco<T, TC>(P.c[ent(a, dn)] + gi);
+            T g = ldco<T, TC>(cptr(P, a, dn) + gi);
             if (!OM1) g *= om;
             acc = fma(-g, __ldcg(P.xnew + gi + (dn ? P.stride[a] : -P.stride[a])), acc);
           }
@@ -431,9 +461,21 @@ __global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
         P.xnew[gi] = acc;
         continue;
       }
-      if (__popc(C) == 1) block_solve<T, TC, KIND, OM1, 1>(P, S, TI, tw, x, y, z, C, tcode);
-      else if (__popc(C) == 2) block_solve<T, TC, KIND, OM1, 2>(P, S, TI, tw, x, y, z, C, tcode);
-      else corner_block<T, TC, KIND, OM1>(P, S, TI, tw, x, y, z, C, tcode);
+      if constexpr (sizeof(T) == 4) {
+        switch (C) {  // the coupled axes as a compile-time mask
+          case 1: block_solve<T, TC, KIND, OM1, 1, 1>(P, S, TI, tw, x, y, z, C, tcode); break;
+          case 2: block_solve<T, TC, KIND, OM1, 1, 2>(P, S, TI, tw, x, y, z, C, tcode); break;
+          case 4: block_solve<T, TC, KIND, OM1, 1, 4>(P, S, TI, tw, x, y, z, C, tcode); break;
+          case 3: block_solve<T, TC, KIND, OM1, 2, 3>(P, S, TI, tw, x, y, z, C, tcode); break;
+          case 5: block_solve<T, TC, KIND, OM1, 2, 5>(P, S, TI, tw, x, y, z, C, tcode); break;
+          case 6: block_solve<T, TC, KIND, OM1, 2, 6>(P, S, TI, tw, x, y, z, C, tcode); break;
+          default: block_solve<T, TC, KIND, OM1, 3, 7>(P, S, TI, tw, x, y, z, C, tcode);
+        }
+      } else {
+        if (__popc(C) == 1) block_solve<T, TC, KIND, OM1, 1>(P, S, TI, tw, x, y, z, C, tcode);
+        else if (__popc(C) == 2) block_solve<T, TC, KIND, OM1, 2>(P, S, TI, tw, x, y, z, C, tcode);
+        else corner_block<T, TC, KIND, OM1>(P, S, TI, tw, x, y, z, C, tcode);
+      }
     }
     __syncthreads();
   }
