@@ -32,6 +32,7 @@ struct P9 {
   int base, coupled;
   const TC* inv;
   const TC* c[8];  // scaled entries W E S N SW SE NW NE
+  int64_t cn;      // c[e] == c[0] + e * cn: entries picked by arithmetic, not by indexing this block
   const T* rhs;
   const T* xold;
   T* xnew;
@@ -87,22 +88,33 @@ __device__ __forceinline__ int slot9(int sub, const int* lc, int w, int h) {
 // The block of own cell (x, y), which lies on the NC coupled start lines C:
 // assembled member by member in canonical order, solved, the own member
 // stored to xnew and the twins to the twin-line store.
-template <class T, class TC, int KIND, bool OM1, int NC>
+// CM = the coupled lines as a compile-time mask (then C == CM), or 0: taken
+// from C at run time; with the mask every axis index is a constant.
+template <class T, class TC, int KIND, bool OM1, int NC, int CM = 0>
 __device__ __forceinline__ T cell9(const P9<T, TC>& P, const Sub9& S, T* tw, int w, int h, int x, int y, int C) {
   const int own[2] = {x, y};
-  int axes[2], nC = 0;
-  for (int a = 0; a < 2; ++a)
-    if (C >> a & 1) axes[nC++] = a;
+  int axes[2] = {0, 0}, nC = 0;
+  if constexpr (CM != 0) {
+    C = CM;
+    axes[0] = (CM & 1) ? 0 : 1;
+    axes[1] = 1;
+    nC = NC;
+  } else {
+    for (int a = 0; a < 2; ++a)
+      if (C >> a & 1) axes[nC++] = a;
+  }
   constexpr int n = 1 << NC;  // nC == NC
   int mo = 0;
-  for (int r = 0; r < nC; ++r)
+#pragma unroll
+  for (int r = 0; r < NC; ++r)
     if (S.c[axes[r]] == 0) mo |= 1 << r;
   T M[n][n], hv[n];
   int64_t gidx[n];
 #pragma unroll
   for (int m = 0; m < n; ++m) {
     int lc[2] = {own[0], own[1]}, sub = 0;
-    for (int r = 0; r < nC; ++r)
+#pragma unroll
+    for (int r = 0; r < NC; ++r)
       if (((m ^ mo) >> r) & 1) {
         lc[axes[r]] = -1;
         sub |= 1 << axes[r];
@@ -144,7 +156,7 @@ __device__ __forceinline__ T cell9(const P9<T, TC>& P, const Sub9& S, T* tw, int
       const int64_t gq = (int64_t)ggy * P.nx + ggx;
       if (upstream && inside) {
         // new value of a cell of the member's own subdomain
-        T g = ldco<T, TC>(P.c[e] + gi);
+        T g = ldco<T, TC>(P.c[0] + e * P.cn + gi);
         if (!OM1) g *= om;
         T v;
         if (sub == 0) {
@@ -160,12 +172,12 @@ __device__ __forceinline__ T cell9(const P9<T, TC>& P, const Sub9& S, T* tw, int
         // face neighbour across a coupled start line: the block partner
         // partner index bit: the coupled axes in order (x before y)
         const int r = NC == 2 ? (dx != 0 ? 0 : 1) : 0;
-        T g = ldco<T, TC>(P.c[e] + gi);
+        T g = ldco<T, TC>(P.c[0] + e * P.cn + gi);
         if (!OM1) g *= om;
         M[m][m ^ (1 << r)] = g;
       } else if (KIND == KIND_SOR) {
         // downstream neighbours, uncoupled or diagonal ones across an interface: old values
-        base = fma(-ldco<T, TC>(P.c[e] + gi), __ldg(P.xold + gq), base);
+        base = fma(-ldco<T, TC>(P.c[0] + e * P.cn + gi), __ldg(P.xold + gq), base);
       }
     }
     T acc;
@@ -202,7 +214,8 @@ __device__ __forceinline__ T cell9(const P9<T, TC>& P, const Sub9& S, T* tw, int
       P.xnew[gidx[m]] = xs[m];
     } else {
       int lc[2] = {own[0], own[1]}, sub = 0;
-      for (int r = 0; r < nC; ++r)
+#pragma unroll
+      for (int r = 0; r < NC; ++r)
         if (((m ^ mo) >> r) & 1) {
           lc[axes[r]] = -1;
           sub |= 1 << axes[r];
@@ -210,7 +223,11 @@ __device__ __forceinline__ T cell9(const P9<T, TC>& P, const Sub9& S, T* tw, int
       tw[slot9(sub, lc, w, h)] = xs[m];
     }
   }
-  return xs[mo];
+  T own_x = xs[0];
+#pragma unroll
+  for (int m = 1; m < n; ++m)
+    if (m == mo) own_x = xs[m];
+  return own_x;
 }
 
 template <class T, class TC, int KIND, bool OM1>
@@ -248,6 +265,8 @@ __global__ void __launch_bounds__(T9) sweep9_kernel(P9<T, TC> P) {
   const int c0 = S.c[0], c1 = S.c[1];
   const int eW = ent9(-1, 0, c0, c1), eSW = ent9(-1, -1, c0, c1), eS = ent9(0, -1, c0, c1),
             eSE = ent9(1, -1, c0, c1);
+  const TC *cW = P.c[0] + eW * P.cn, *cSW = P.c[0] + eSW * P.cn, *cS = P.c[0] + eS * P.cn,
+           *cSE = P.c[0] + eSE * P.cn;
   const T om = OM1 ? T(1) : P.om[c0 | (c1 << 1)];
   const int y = lt;
   T ni = T(0), nr = T(0), ng[4] = {T(0), T(0), T(0), T(0)};  // next level's operands
@@ -258,10 +277,10 @@ __global__ void __launch_bounds__(T9) sweep9_kernel(P9<T, TC> P) {
     const int64_t gi = (int64_t)S.gco(1, y) * P.nx + S.gco(0, x2);
     if (KIND == KIND_TRI_SCALED) ni = ldco<T, TC>(P.inv + gi);
     nr = __ldg(P.rhs + gi);
-    ng[0] = x2 >= 1 ? ldco<T, TC>(P.c[eW] + gi) : T(0);
-    ng[1] = (x2 >= 1 && y >= 1) ? ldco<T, TC>(P.c[eSW] + gi) : T(0);
-    ng[2] = y >= 1 ? ldco<T, TC>(P.c[eS] + gi) : T(0);
-    ng[3] = (x2 + 1 < w && y >= 1) ? ldco<T, TC>(P.c[eSE] + gi) : T(0);
+    ng[0] = x2 >= 1 ? ldco<T, TC>(cW + gi) : T(0);
+    ng[1] = (x2 >= 1 && y >= 1) ? ldco<T, TC>(cSW + gi) : T(0);
+    ng[2] = y >= 1 ? ldco<T, TC>(cS + gi) : T(0);
+    ng[3] = (x2 + 1 < w && y >= 1) ? ldco<T, TC>(cSE + gi) : T(0);
   };
   T xr = T(0);
   fetch(0);
@@ -303,9 +322,11 @@ __global__ void __launch_bounds__(T9) sweep9_kernel(P9<T, TC> P) {
           P.xnew[(int64_t)S.gco(1, y) * P.nx + S.gco(0, x)] = acc;
           v = acc;
         } else if (C == 3) {
-          v = cell9<T, TC, KIND, OM1, 2>(P, S, tw, w, h, x, y, C);
+          v = cell9<T, TC, KIND, OM1, 2, 3>(P, S, tw, w, h, x, y, C);
+        } else if (C == 1) {
+          v = cell9<T, TC, KIND, OM1, 1, 1>(P, S, tw, w, h, x, y, C);
         } else {
-          v = cell9<T, TC, KIND, OM1, 1>(P, S, tw, w, h, x, y, C);
+          v = cell9<T, TC, KIND, OM1, 1, 2>(P, S, tw, w, h, x, y, C);
         }
         ring[(L & 3) * h + y] = v;
         xr = v;
@@ -374,6 +395,7 @@ P9<T, TC> params9(Handle* h, int mode, int64_t t, const ScaledSet& set, const vo
   const TC* b = (const TC*)set.base;
   P.inv = b;
   for (int e = 0; e < 8; ++e) P.c[e] = b + (size_t)(1 + e) * N;
+  P.cn = (int64_t)N;
   P.rhs = (const T*)rhs;
   P.xold = (const T*)xold;
   P.xnew = (T*)xnew;
