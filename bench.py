@@ -433,6 +433,16 @@ def workload_poisson3d(args):
         out[prec] = {"ssor_apply_ms": apply_ms, "sweep_gcell_per_s": 2 * N / apply_ms / 1e6,
                      **{k: info[k] for k in ("iters", "outer", "relres", "wall_s")}}
         h.close()
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        pb = oracle.Problem(3, p["n"], 7, p["diags"], p["sub"])
+        pb.ssor_apply(oracle.DECOMPOSED, 1.0, p["b"])  # builds the sweep plan
+        t0 = time.perf_counter()
+        pb.ssor_apply(oracle.DECOMPOSED, 1.0, p["b"])
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": 2 * N / dt / 1e9, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
+                               "sample": f"one fp64 SSOR apply (two sweeps) of the oracle at {n}^3 ({dt:.1f} s)"}
     print(json.dumps({"workload": f"poisson3d-{n}^3-7pt-ssor-pcg-{max(1, n // 32)}^3", "metric": "solve seconds to rel-res 1e-8",
                       **out}))
 
@@ -585,13 +595,24 @@ def workload_mg2048(args):
     x = torch.zeros_like(b)
     ilu = _timed_solve(torch, h, nd.BICGSTAB, nd.PREC_ILU0, b, x, rtol=1e-8, maxit=20000)
     h.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        import oracle.mg as omg
+        oracle.build()
+        H = omg.Hierarchy(n, n, p["diags"], p["sub"], om)
+        t0 = time.perf_counter()
+        H.vcycle(p["b"])
+        dt = time.perf_counter() - t0
+        cpu = {"value": dt * 1e3, "unit": "ms per V-cycle", "cores": 1, "kind": "oracle",
+               "sample": f"one V-cycle of the oracle (oracle/mg.py) on the same 2048^2 hierarchy ({dt:.1f} s)"}
     print(json.dumps({"workload": f"varcoef2d-{n}x{n}-5pt-fp64-mg-pcg-16x16", "metric": "solve seconds to rel-res 1e-8",
                       "mg_pcg": {"iters": info["iters"], "relres": info["relres"], "wall_s": float(np.median(walls)),
                                  "levels": levels, "omega": om, "vcycle_ms": vc_ms},
                       "vcycle_roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                                           "frac": gbs / peak, "peak_kind": kind,
                                           "kernel": "one V-cycle (sweep2d SSOR applies, residuals, transfers)"},
-                      "bicgstab_ilu0": {k: ilu[k] for k in ("iters", "relres", "wall_s")}}))
+                      "bicgstab_ilu0": {k: ilu[k] for k in ("iters", "relres", "wall_s")}, "cpu_baseline": cpu}))
 
 
 def workload_eikonal2048(args):
@@ -630,6 +651,18 @@ def workload_eikonal2048(args):
             host_walls.append(hinfo["seconds"])
     e.close()
     N = n * n
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        E = oracle.Eikonal(p["n"], p["h"], p["f"], p["sub"])
+        u = p["u0"]
+        t0 = time.perf_counter()
+        for t in range(8):
+            u, _ = E.sweep(t, u)
+        dt = (time.perf_counter() - t0) / 8
+        cpu = {"value": N / dt / 1e9, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"8 decomposed sweeps of the oracle on the same 2048^2 problem ({dt * 1e3:.0f} ms each)"}
     peak, kind = measured_peaks()
     gbs = 24.0 * N / (sweep_ms / 1e3) / 1e9  # u_old and f read, u_new written, 8 B each
     # the update is fp64 arithmetic: 14 operations a cell on its two-sided
@@ -644,7 +677,8 @@ def workload_eikonal2048(args):
                       "roofline": {"bound": "alu", "achieved": gops, "peak": 625.0, "unit": "Gop/s (fp64)",
                                    "frac": gops / 625.0, "peak_kind": "nominal fp64 rate",
                                    "kernel": "eik_sweep_kernel"},
-                      "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_kind": kind}}))
+                      "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_kind": kind},
+                      "cpu_baseline": cpu}))
 
 
 EXTRA = {"poisson64": workload_poisson64, "poisson3d": workload_poisson3d,
