@@ -174,3 +174,30 @@ def test_sweeps3d_reduced_precision(nd, prec, tol):
     h.ilu0_apply(_t(b, f32), z)
     assert _rel(z.cpu().numpy(), ref.ilu0_apply(b)) <= tol
     h.close()
+
+
+def test_full_size_applies_match_oracle(nd):
+    """The 256^3 Poisson workload with 8 x 8 x 8 subdomains, in the launch
+    configuration the benchmark times: the fp64 SSOR apply and the decomposed
+    ILU(0) apply element by element against the oracle (1e-12), and the fp32
+    SSOR apply (2e-5)."""
+    import torch
+    p = W.poisson3d_problem()
+    N = int(np.prod(p["n"]))
+    r = p["b"]
+    ref = oracle.Problem(3, p["n"], 7, p["diags"], p["sub"])
+    want = ref.ssor_apply(oracle.DECOMPOSED, 1.0, r)
+    h = nd.NDiag(3, p["n"], 7, p["diags"], p["sub"], "fp64")
+    z = _t(np.zeros(N))
+    h.ssor_apply(1.0, _t(r), z)
+    assert _rel(z.cpu().numpy(), want) <= 1e-12
+    h.ilu0_factor(nd.DECOMPOSED)
+    h.ilu0_apply(_t(r), z)
+    ref.ilu0_factor(oracle.DECOMPOSED)
+    assert _rel(z.cpu().numpy(), ref.ilu0_apply(r)) <= 1e-12
+    h.close()
+    h32 = nd.NDiag(3, p["n"], 7, p["diags"], p["sub"], "fp32")
+    z32 = _t(np.zeros(N), torch.float32)
+    h32.ssor_apply(1.0, _t(r, torch.float32), z32)
+    assert _rel(z32.cpu().numpy(), want) <= 2e-5
+    h32.close()
