@@ -179,7 +179,7 @@ def main():
                     help="only factor and run K ILU(0) applies of the workload (for kernel profiling)")
     ap.add_argument("--workload", default="varcoef2048",
                     choices=["varcoef2048", "poisson64", "poisson3d", "batch512", "serving", "mg2048",
-                             "eikonal2048"],
+                             "eikonal2048", "mg3d"],
                     help="varcoef2048 is the benchmark; the others print one measurement line each")
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--n3d", type=int, default=256, help="side of the 3D Poisson workload (subdomains of 32^3)")
@@ -681,9 +681,60 @@ def workload_eikonal2048(args):
                       "cpu_baseline": cpu}))
 
 
+def workload_mg3d(args):
+    """The 256^3 Poisson workload (8 x 8 x 8 subdomains, fp64) solved by PCG
+    with the 3D multigrid V-cycle (decomposed SSOR smoother, omega 0.9), beside
+    SSOR-PCG on the same handle. V-cycle time with CUDA events around whole
+    cycles."""
+    import numpy as np
+    torch, nd, W = _setup()
+    n = args.n3d
+    p = W.poisson3d_problem(n, max(1, n // 32))
+    om = 0.9
+    h = nd.NDiag(3, p["n"], 7, p["diags"], p["sub"], "fp64")
+    b = torch.tensor(p["b"], device="cuda")
+    z = torch.empty_like(b)
+    for _ in range(3):
+        h.mg_apply(om, b, z)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(5):
+        h.mg_apply(om, b, z)
+    e1.record()
+    torch.cuda.synchronize()
+    vc_ms = e0.elapsed_time(e1) / 5
+    walls = []
+    for k in range(args.warmup + max(1, args.steps)):
+        x = torch.zeros_like(b)
+        info = _timed_solve(torch, h, nd.PCG, nd.PREC_MG, b, x, rtol=1e-8, maxit=500, omega=om)
+        if k >= args.warmup:
+            walls.append(info["wall_s"])
+    x = torch.zeros_like(b)
+    ssor = _timed_solve(torch, h, nd.PCG, nd.PREC_SSOR, b, x, rtol=1e-8, maxit=5000)
+    levels = h.mg_levels()
+    h.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        import oracle.mg as omg
+        oracle.build()
+        H = omg.Hierarchy3(p["n"], p["diags"], p["sub"], om)
+        t0 = time.perf_counter()
+        H.vcycle(p["b"])
+        dt = time.perf_counter() - t0
+        cpu = {"value": dt * 1e3, "unit": "ms per V-cycle", "cores": 1, "kind": "oracle",
+               "sample": f"one V-cycle of the oracle (oracle/mg.py) on the same {n}^3 hierarchy ({dt:.1f} s)"}
+    print(json.dumps({"workload": f"poisson3d-{n}^3-7pt-fp64-mg-pcg-{max(1, n // 32)}^3",
+                      "metric": "solve seconds to rel-res 1e-8",
+                      "mg_pcg": {"iters": info["iters"], "relres": info["relres"], "wall_s": float(np.median(walls)),
+                                 "levels": levels, "omega": om, "vcycle_ms": vc_ms},
+                      "ssor_pcg": {k: ssor[k] for k in ("iters", "relres", "wall_s")}, "cpu_baseline": cpu}))
+
+
 EXTRA = {"poisson64": workload_poisson64, "poisson3d": workload_poisson3d,
          "batch512": workload_batch512, "serving": workload_serving, "mg2048": workload_mg2048,
-         "eikonal2048": workload_eikonal2048}
+         "eikonal2048": workload_eikonal2048, "mg3d": workload_mg3d}
 
 
 if __name__ == "__main__":

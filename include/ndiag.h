@@ -140,17 +140,18 @@ ndiag_status ssor_apply(ndiag* h, int mode, double omega, const void* r, void* z
  *     z += 1.8 P_k B_{k+1} P_k^T (r - A_k z)
  *     z += S_k (r - A_k z)
  * S_k = ssor_apply(DECOMPOSED, omega) of level k; P_k = piecewise-constant
- * prolongation over 2 x 2 cell aggregates (x // 2, y // 2); A_{k+1} =
- * P_k^T A_k P_k (5-point again), split into min(16, max(1, nx / 16)) x
- * min(16, max(1, ny / 16)) subdomains; coarsening stops when both sides are <= 32 cells or at 10
- * levels; the coarsest level takes 4 steps of SSOR-Richardson. B is symmetric;
+ * prolongation over 2 x 2 cell aggregates (x // 2, y // 2), in 3D 2 x 2 x 2
+ * (z // 2 as well); A_{k+1} = P_k^T A_k P_k (5-point / 7-point again), split
+ * into min(16, max(1, n / 16)) parts per axis (3D: min(8, max(1, n / 16)));
+ * coarsening stops when every side is <= 32 cells (3D: 16) or at 10 levels;
+ * the coarsest level takes 4 steps of SSOR-Richardson. B is symmetric;
  * it is positive definite when S contracts in the A-norm, which for subdomains
  * meeting at interior vertices needs omega < 1.
  *   r, z  fp64 DEVICE vectors of N values, z must not alias r.
  * The first call builds the hierarchy on the host from the handle's matrix
  * (a blocking device-to-host copy), later calls are asynchronous.
- * Errors: NDIAG_EINVAL (not a 2D 5-point fp64 handle, omega outside (0, 2)),
- * NDIAG_ENOMEM.
+ * Errors: NDIAG_EINVAL (not a 2D 5-point or 3D 7-point fp64 handle, omega
+ * outside (0, 2)), NDIAG_ENOMEM.
  */
 ndiag_status mg_apply(ndiag* h, double omega, const double* r, double* z);
 
@@ -282,11 +283,11 @@ typedef struct {
  *           MG: one symmetric multigrid V-cycle with the decomposed SSOR apply
  *           (factor omega[0]) as pre- and post-smoother on every level (the
  *           sweep as a multigrid smoother, Sec. 5). Coarse levels are the
- *           Galerkin products P^T A P over 2 x 2 cell aggregates
- *           (piecewise-constant P, so every level stays 5-point), down to a
- *           grid of at most 32 cells per side, where 4 SSOR steps are taken.
- *           2D 5-point fp64 handles and DECOMPOSED mode only (else
- *           NDIAG_EINVAL). The hierarchy is built on the host from the
+ *           Galerkin products P^T A P over 2 x 2 (x 2) cell aggregates
+ *           (piecewise-constant P, so every level stays 5-point / 7-point),
+ *           down to a grid of at most 32 (3D: 16) cells per side, where 4 SSOR
+ *           steps are taken. 2D 5-point and 3D 7-point fp64 handles and
+ *           DECOMPOSED mode only (else NDIAG_EINVAL). The hierarchy is built on the host from the
  *           handle's matrix on the first MG solve, kept on the handle and
  *           freed by ndiag_destroy.
  *   mode    NDIAG_DECOMPOSED or NDIAG_NATURAL ordering of the sweeps.

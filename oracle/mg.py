@@ -38,9 +38,13 @@ cycle used as a PCG preconditioner, written in the plainest form:
 
 The sparse products are scipy's (a library primitive standing for P^T A P);
 the SSOR apply and the matrix-vector product are the C++ oracle's.
+The 3D 7-point cycle (Hierarchy3) is the same with 2 x 2 x 2 aggregates,
+coarsening while a side exceeds 16 cells and coarse parts min(8, max(1, n // 16)).
+
 Pins: tests/test_oracle_mg.py (dense P^T A P, the closed form of the Poisson
 coarse stencil, the dense error-propagation form of the two-level cycle, the
-closed form of SSOR-Richardson, symmetry and definiteness).
+closed form of SSOR-Richardson, symmetry and definiteness; the 3D cycle's
+Galerkin product, coarse stencil, two-level form and smoother bound).
 """
 from __future__ import annotations
 
@@ -131,9 +135,13 @@ class Hierarchy:
             for _ in range(KC - 1):
                 z = z + self.smooth(k, r - pb.matvec(z))
             return z
-        P = prolongation(nx, ny)
+        P = self.prolong(k)
         z = z + ALPHA * (P @ self.vcycle(P.T @ (r - pb.matvec(z)), k + 1))
         return z + self.smooth(k, r - pb.matvec(z))
+
+    def prolong(self, k):
+        nx, ny, _ = self.levels[k]
+        return prolongation(nx, ny)
 
 
 def pcg(H: Hierarchy, b, rtol, maxit, x0=None):
@@ -177,3 +185,88 @@ def pcg(H: Hierarchy, b, rtol, maxit, x0=None):
             return x, dict(iters=it, relres=tr, status=1)
         if tr <= rtol:
             return x, dict(iters=it, relres=tr, status=0)
+
+
+# --- 3D 7-point ------------------------------------------------------------
+# The same cycle on 7-point matrices (entries C W E S N B F, x fastest):
+# 2 x 2 x 2 aggregates (one cell wide at an odd side's end), coarsening while a
+# side exceeds NMIN3, coarse levels split into coarse_parts3(n) parts per axis.
+
+NMIN3 = 16
+
+
+def coarse_parts3(n: int) -> int:
+    """Subdomains along an axis of n cells on a coarse 3D level."""
+    return min(8, max(1, n // 16))
+
+
+_OFF7 = ((0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1))
+
+
+def prolongation3(n) -> sp.csr_matrix:
+    """P (N x Nc): P[i, I] = 1 when fine cell i lies in aggregate I."""
+    nx, ny, nz = n
+    nxc, nyc, nzc = (nx + 1) // 2, (ny + 1) // 2, (nz + 1) // 2
+    i = np.arange(nx * ny * nz)
+    x, y, z = i % nx, (i // nx) % ny, i // (nx * ny)
+    I = ((z // 2) * nyc + y // 2) * nxc + x // 2
+    return sp.csr_matrix((np.ones(i.size), (i, I)), shape=(i.size, nxc * nyc * nzc))
+
+
+def to_sparse3(n, diags: np.ndarray) -> sp.csr_matrix:
+    """The 7-point matrix of diagonal-major entries."""
+    nx, ny, nz = n
+    N = nx * ny * nz
+    i = np.arange(N)
+    x, y, z = i % nx, (i // nx) % ny, i // (nx * ny)
+    rows, cols, vals = [], [], []
+    for k, (dx, dy, dz) in enumerate(_OFF7):
+        ok = (x + dx >= 0) & (x + dx < nx) & (y + dy >= 0) & (y + dy < ny) & (z + dz >= 0) & (z + dz < nz)
+        rows.append(i[ok])
+        cols.append(i[ok] + dx + nx * (dy + ny * dz))
+        vals.append(diags[k][ok])
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N))
+
+
+def from_sparse3(n, A: sp.spmatrix) -> np.ndarray:
+    """Diagonal-major 7-point entries of A; raises if A has entries elsewhere."""
+    nx, ny, nz = n
+    A = sp.coo_matrix(A)
+    r, c = A.row.astype(np.int64), A.col.astype(np.int64)
+    dx = c % nx - r % nx
+    dy = (c // nx) % ny - (r // nx) % ny
+    dz = c // (nx * ny) - r // (nx * ny)
+    k = np.full(r.shape, -1)
+    for kk, (ox, oy, oz) in enumerate(_OFF7):
+        k[(dx == ox) & (dy == oy) & (dz == oz)] = kk
+    if np.any((k < 0) & (A.data != 0.0)):
+        raise ValueError("coarse operator left the 7-point pattern")
+    d = np.zeros((7, nx * ny * nz))
+    keep = k >= 0
+    np.add.at(d, (k[keep], r[keep]), A.data[keep])
+    return d
+
+
+def galerkin3(n, diags: np.ndarray) -> np.ndarray:
+    """A_c = P^T A P as diagonal-major 7-point entries of the coarse grid."""
+    P = prolongation3(n)
+    C = (P.T @ to_sparse3(n, diags) @ P).tocoo()
+    return from_sparse3(tuple((v + 1) // 2 for v in n), C)
+
+
+class Hierarchy3(Hierarchy):
+    """Levels (n, None, oracle.Problem) of a 3D 7-point problem."""
+
+    def __init__(self, n, diags, sub, omega, library=None):
+        self.omega = float(omega)
+        n = tuple(int(v) for v in n)
+        self.levels = [(n, None, oracle.Problem(3, n, 7, diags, tuple(sub), library=library))]
+        d = np.asarray(diags, dtype=np.float64).reshape(7, int(np.prod(n)))
+        while max(n) > NMIN3 and len(self.levels) < LMAX:
+            d = galerkin3(n, d)
+            n = tuple((v + 1) // 2 for v in n)
+            sub_c = tuple(coarse_parts3(v) for v in n)
+            self.levels.append((n, None, oracle.Problem(3, n, 7, d, sub_c, library=library)))
+
+    def prolong(self, k):
+        return prolongation3(self.levels[k][0])

@@ -306,9 +306,10 @@ extern "C" ndiag_status krylov_solve(ndiag* h, int method, int precond, int mode
   if (method < NDIAG_PCG || method > NDIAG_STATIONARY) return NDIAG_EINVAL;
   if (precond < NDIAG_PREC_NONE || precond > NDIAG_PREC_MG) return NDIAG_EINVAL;
   if (method != NDIAG_STATIONARY && precond == NDIAG_PREC_MG &&
-      (h->dim != 2 || h->stencil != 5 || h->precision != NDIAG_FP64 || mode != NDIAG_DECOMPOSED ||
-       !(omega[0] > 0.0 && omega[0] < 2.0))) {
-    set_error("the multigrid preconditioner needs a 2D 5-point fp64 handle, DECOMPOSED mode and 0 < omega < 2");
+      (!((h->dim == 2 && h->stencil == 5) || (h->dim == 3 && h->stencil == 7)) || h->precision != NDIAG_FP64 ||
+       mode != NDIAG_DECOMPOSED || !(omega[0] > 0.0 && omega[0] < 2.0))) {
+    set_error("the multigrid preconditioner needs a 2D 5-point or 3D 7-point fp64 handle, DECOMPOSED mode "
+              "and 0 < omega < 2");
     return NDIAG_EINVAL;
   }
   if (mode != NDIAG_NATURAL && mode != NDIAG_DECOMPOSED) return NDIAG_EINVAL;

@@ -6,6 +6,7 @@ Nothing here touches the CUDA library. Usage:
     python tests/golden/make_golden.py varcoef2048 # long: two full 2048^2 solves
     python tests/golden/make_golden.py varcoef2048_envelope  # long: 7 perturbed solves in parallel
     python tests/golden/make_golden.py varcoef2048_mg  # long: one 2048^2 multigrid-PCG solve
+    python tests/golden/make_golden.py poisson3d256_mg  # long: one 256^3 multigrid-PCG solve (about 10 GB)
 Output: tests/golden/<name>.json
 """
 import json
@@ -62,6 +63,19 @@ def varcoef2048_mg(n=2048, sub=16, omega=0.9):
     return out
 
 
+def poisson3d256_mg(n=256, sub=8, omega=0.9):
+    """Oracle 3D multigrid-PCG (oracle/mg.py) on the 256^3 Poisson workload."""
+    import oracle.mg as mg
+    p = W.poisson3d_problem(n, sub)
+    t0 = time.time()
+    H = mg.Hierarchy3(p["n"], p["diags"], p["sub"], omega)
+    x, info = mg.pcg(H, p["b"], 1e-8, 500)
+    out = dict(omega=omega, levels=len(H.levels), iters=info["iters"], relres=info["relres"],
+               status=info["status"], seconds=time.time() - t0, x_norm=float(np.linalg.norm(x)))
+    print(out, flush=True)
+    return out
+
+
 def _perturbed_solve(k, n=2048, sub=16):
     """Oracle BiCGSTAB count of the 2048^2 workload with b scaled by
     (1 + 1e-15 g), g ~ N(0, 1) from seed 4242 + k (rounding-level change)."""
@@ -86,7 +100,7 @@ def varcoef2048_envelope(count=7):
 
 
 JOBS = {"poisson64": poisson64, "varcoef2048": varcoef2048, "varcoef2048_envelope": varcoef2048_envelope,
-        "varcoef2048_mg": varcoef2048_mg}
+        "varcoef2048_mg": varcoef2048_mg, "poisson3d256_mg": poisson3d256_mg}
 
 if __name__ == "__main__":
     oracle.build()

@@ -3,7 +3,7 @@ krylov_solve with NDIAG_PREC_MG) against the oracle's cycle (oracle/mg.py):
 one V-cycle element by element, the hierarchy's levels, PCG iteration counts
 within one, the argument checks, and at full size (2048^2, 16 x 16 subdomains)
 one V-cycle element by element and the solve's iteration count against the
-stored oracle count."""
+stored oracle count; the 3D 7-point cycle likewise on 3D grids."""
 import json
 import os
 
@@ -117,11 +117,16 @@ def test_refused_configurations(nd):
         h.mg_apply(2.0, b, x)
     assert h.mg_levels() == 0
     h.close()
-    h3 = nd.NDiag(3, (16, 16, 16), 7, W.poisson3d(16, 16, 16), (2, 2, 2), "fp64")
+    h3 = nd.NDiag(3, (16, 16, 16), 7, W.poisson3d(16, 16, 16), (2, 2, 2), "fp32")
     b3 = torch.ones(16 ** 3, dtype=torch.float64, device="cuda")
     with pytest.raises(nd.NdiagError):
         h3.solve(nd.PCG, nd.PREC_MG, b3, torch.zeros_like(b3), omega=0.9)
     h3.close()
+    h9 = nd.NDiag(2, (20, 20), 9, W.convdiff9(20, 1.0, 0.3), (2, 2), "fp64")
+    b9 = torch.ones(400, dtype=torch.float64, device="cuda")
+    with pytest.raises(nd.NdiagError):
+        h9.solve(nd.PCG, nd.PREC_MG, b9, torch.zeros_like(b9), omega=0.9)
+    h9.close()
 
 
 def test_full_size_vcycle_and_count(nd):
@@ -146,6 +151,97 @@ def test_full_size_vcycle_and_count(nd):
     bd = torch.tensor(p["b"], device="cuda")
     x = torch.zeros_like(bd)
     res = h.solve(nd.PCG, nd.PREC_MG, bd, x, rtol=1e-8, maxit=2000, omega=om)
+    h.close()
+    assert res["relres"] <= 1e-8
+    assert abs(res["iters"] - g["iters"]) <= 1, (res, g)
+
+
+CASES3 = [
+    ((40, 36, 30), (2, 2, 2), 0.9, 51),   # 3 levels
+    ((33, 31, 29), (3, 2, 2), 0.85, 52),  # odd sides, interior start vertices
+    ((64, 20, 18), (4, 1, 1), 0.9, 53),   # slabs
+]
+
+
+def _matrix3(n, seed):
+    """SPD 7-point matrix from random face conductances (lognormal)."""
+    g = np.random.default_rng(seed)
+    nx, ny, nz = n
+    N = nx * ny * nz
+    d = np.zeros((7, N))
+    idx = np.arange(N).reshape(nz, ny, nx)
+    for a, (lo, hi) in enumerate(((1, 2), (3, 4), (5, 6))):
+        ax = 2 - a
+        sl_lo, sl_hi = [slice(None)] * 3, [slice(None)] * 3
+        sl_lo[ax], sl_hi[ax] = slice(0, -1), slice(1, None)
+        i_lo, i_hi = idx[tuple(sl_lo)].ravel(), idx[tuple(sl_hi)].ravel()
+        k = np.exp(0.5 * g.standard_normal(i_lo.size))
+        d[hi, i_lo] = -k
+        d[lo, i_hi] = -k
+    d[0] = -d[1:].sum(axis=0) + 0.01
+    return d
+
+
+@pytest.mark.parametrize("n,sub,om,seed", CASES3)
+def test_vcycle3_matches_oracle(nd, n, sub, om, seed):
+    import torch
+    d = _matrix3(n, seed)
+    N = int(np.prod(n))
+    r = np.random.default_rng(seed).standard_normal(N)
+    H = M.Hierarchy3(n, d, sub, om)
+    want = H.vcycle(r)
+    h = nd.NDiag(3, n, 7, d, sub, "fp64")
+    rd = torch.tensor(r, device="cuda")
+    z = torch.empty_like(rd)
+    h.mg_apply(om, rd, z)
+    assert h.mg_levels() == len(H.levels)
+    err = np.abs(z.cpu().numpy() - want).max() / np.abs(want).max()
+    h.close()
+    assert err <= VTOL, err
+
+
+def test_pcg_mg3_matches_oracle_count(nd):
+    import torch
+    n, sub, om = (40, 36, 30), (2, 2, 2), 0.9
+    d = _matrix3(n, 54)
+    b = W.uniform_rhs(int(np.prod(n)), 55)
+    H = M.Hierarchy3(n, d, sub, om)
+    xr, info = M.pcg(H, b, 1e-8, 300)
+    assert info["status"] == 0
+    h = nd.NDiag(3, n, 7, d, sub, "fp64")
+    bd = torch.tensor(b, device="cuda")
+    x = torch.zeros_like(bd)
+    res = h.solve(nd.PCG, nd.PREC_MG, bd, x, rtol=1e-8, maxit=300, omega=om)
+    h.close()
+    assert res["relres"] <= 1e-8
+    assert abs(res["iters"] - info["iters"]) <= 1, (res, info)
+
+
+def test_full_size_vcycle3_and_count(nd):
+    """256^3 Poisson with 8 x 8 x 8 subdomains, the configuration bench.py's
+    3D multigrid line times: one V-cycle element by element against the
+    oracle's, and the PCG count against the stored oracle count."""
+    import torch
+    p = W.poisson3d_problem()
+    om = 0.9
+    H = M.Hierarchy3(p["n"], p["diags"], p["sub"], om)
+    want = H.vcycle(p["b"])
+    h = nd.NDiag(3, p["n"], 7, p["diags"], p["sub"], "fp64")
+    bd = torch.tensor(p["b"], device="cuda")
+    z = torch.empty_like(bd)
+    h.mg_apply(om, bd, z)
+    err = np.abs(z.cpu().numpy() - want).max() / np.abs(want).max()
+    assert err <= VTOL, err
+    assert h.mg_levels() == len(H.levels)
+    del H
+    path = os.path.join(os.path.dirname(__file__), "golden", "poisson3d256_mg.json")
+    if not os.path.exists(path):
+        h.close()
+        pytest.skip("no stored oracle count (tests/golden/make_golden.py poisson3d256_mg)")
+    g = json.load(open(path))
+    assert g["omega"] == om
+    x = torch.zeros_like(bd)
+    res = h.solve(nd.PCG, nd.PREC_MG, bd, x, rtol=1e-8, maxit=500, omega=om)
     h.close()
     assert res["relres"] <= 1e-8
     assert abs(res["iters"] - g["iters"]) <= 1, (res, g)

@@ -251,3 +251,100 @@ def test_pins_catch_planted_mistake(anchor, replacement):
     mod = types.ModuleType("mg_mutant")
     exec(compile(src.replace(anchor, replacement), "mg_mutant", "exec"), mod.__dict__)
     assert not (_pin_galerkin(mod) and _pin_coarsest(mod) and _pin_two_level(mod))
+
+
+# --- 3D 7-point cycle ------------------------------------------------------------
+
+def _rand7(n, seed):
+    g = np.random.default_rng(seed)
+    N = int(np.prod(n))
+    d = -g.uniform(0.2, 1.0, size=(7, N))
+    d = W._zero_outside(d, n, 7)
+    d[0] = -d[1:].sum(axis=0) + g.uniform(0.05, 0.5, size=N)
+    return d
+
+
+def _dense_P3(n):
+    nx, ny, nz = n
+    nc = [(v + 1) // 2 for v in n]
+    P = np.zeros((nx * ny * nz, nc[0] * nc[1] * nc[2]))
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                P[(z * ny + y) * nx + x, ((z // 2) * nc[1] + y // 2) * nc[0] + x // 2] = 1.0
+    return P
+
+
+def _dense3(n, d):
+    return assemble(n, 7, d).toarray()
+
+
+@pytest.mark.parametrize("n", [(5, 4, 3), (4, 4, 4), (3, 1, 5)])
+def test_galerkin3_matches_dense_product(n):
+    d = _rand7(n, sum(n))
+    P = _dense_P3(n)
+    nc = tuple((v + 1) // 2 for v in n)
+    np.testing.assert_allclose(_dense3(nc, M.galerkin3(n, d)), P.T @ _dense3(n, d) @ P, rtol=0, atol=1e-13)
+
+
+def test_galerkin3_poisson_closed_form():
+    # 2 x 2 x 2 aggregates of the 7-point Laplacian (6, -1): centre 8*6 - 24 = 24,
+    # four unit couplings cross each aggregate face (-4)
+    n = (8, 6, 4)
+    dc = M.galerkin3(n, W.poisson3d(*n))
+    nc = (4, 3, 2)
+    I = np.arange(np.prod(nc))
+    X, Y, Z = I % nc[0], (I // nc[0]) % nc[1], I // (nc[0] * nc[1])
+    np.testing.assert_array_equal(dc[0], np.full(I.size, 24.0))
+    for k, (c, lim, sgn) in enumerate(((X, nc[0], -1), (X, nc[0], 1), (Y, nc[1], -1), (Y, nc[1], 1),
+                                       (Z, nc[2], -1), (Z, nc[2], 1)), start=1):
+        inside = (c > 0) if sgn < 0 else (c < lim - 1)
+        np.testing.assert_array_equal(dc[k], np.where(inside, -4.0, 0.0))
+
+
+def test_two_level_cycle3_error_propagation():
+    n, om = (10, 8, 8), 0.85
+    d = _rand7(n, 77)
+    M.NMIN3, saved = 5, M.NMIN3  # two levels: 10 x 8 x 8 -> 5 x 4 x 4
+    try:
+        H = M.Hierarchy3(n, d, (2, 2, 2), om)
+    finally:
+        M.NMIN3 = saved
+    assert len(H.levels) == 2
+    N = int(np.prod(n))
+    pb, (nc, _, pc) = H.levels[0][2], H.levels[1]
+    Nc = int(np.prod(nc))
+    S = _dense_op(lambda e: pb.ssor_apply(oracle.DECOMPOSED, om, e), N)
+    Sc = _dense_op(lambda e: pc.ssor_apply(oracle.DECOMPOSED, om, e), Nc)
+    A = _dense3(n, d)
+    P = _dense_P3(n)
+    Ac = P.T @ A @ P
+    Bc = (np.eye(Nc) - np.linalg.matrix_power(np.eye(Nc) - Sc @ Ac, M.KC)) @ np.linalg.inv(Ac)
+    I = np.eye(N)
+    E = (I - S @ A) @ (I - M.ALPHA * P @ Bc @ P.T @ A) @ (I - S @ A)
+    r = np.random.default_rng(8).standard_normal(N)
+    want = (I - E) @ np.linalg.solve(A, r)
+    np.testing.assert_allclose(H.vcycle(r), want, rtol=0, atol=1e-10 * np.abs(want).max())
+
+
+def test_smoother3_bound_at_omega_one():
+    # an interior vertex where eight subdomains start: the 2 x 2 x 2 corner block
+    # of the 7-point Laplacian gives S A the eigenvalue 6 / (6 - 3) = 2
+    n = (12, 12, 12)
+    N = int(np.prod(n))
+    d = W.poisson3d(*n)
+    pb = oracle.Problem(3, n, 7, d, (3, 3, 3))
+    A = _dense3(n, d)
+    S = _dense_op(lambda e: pb.ssor_apply(oracle.DECOMPOSED, 1.0, e), N)
+    assert abs(np.linalg.eigvals(S @ A).real.max() - 2.0) < 1e-9
+    S9 = _dense_op(lambda e: pb.ssor_apply(oracle.DECOMPOSED, 0.9, e), N)
+    assert np.linalg.eigvals(S9 @ A).real.max() < 2.0
+
+
+def test_hierarchy3_shape_and_pcg():
+    p = W.poisson3d_problem(48, 3)
+    H = M.Hierarchy3(p["n"], p["diags"], p["sub"], 0.9)
+    assert [lv[0] for lv in H.levels] == [(48, 48, 48), (24, 24, 24), (12, 12, 12)]
+    assert [lv[2].sub for lv in H.levels] == [(3, 3, 3), (1, 1, 1), (1, 1, 1)]
+    x, info = M.pcg(H, p["b"], 1e-8, 100)
+    assert info["status"] == 0 and info["iters"] <= 20
