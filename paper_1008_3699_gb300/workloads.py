@@ -193,6 +193,14 @@ def poisson3d_problem(n: int = 256, sub: int = 8, seed: int = 1003):
                 b=uniform_rhs(n ** 3, seed), sub=(sub, sub, sub))
 
 
+def embed5in9(diags5: np.ndarray) -> np.ndarray:
+    """The same matrix in 9-point storage (C W E S N SW SE NW NE), the four
+    diagonal entries zero."""
+    d = np.zeros((9, diags5.shape[1]))
+    d[:5] = diags5
+    return d
+
+
 def eikonal_problem(n: int = 2048, sub: int = 16, seed: int = 1006, sources: int = 4):
     """Travel times on an n x n grid of the unit square (h = 1/n) through a
     heterogeneous medium: slowness f = box5x5(exp(N(0, 1))) per cell, `sources`
