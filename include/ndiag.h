@@ -229,7 +229,10 @@ ndiag_status eikonal_solve(ndiag_eik* e, double* u, double delta, int max_rounds
  * with one lexicographic subdomain for 5/7-point matrices; for 9-point
  * matrices the true ILU(0) of the lexicographic order, whose off-diagonal
  * entries are modified too (IKJ elimination on the 9-point pattern, Saad
- * Alg. 10.4), applied as (D + L') D^-1 (D + U') with D = diag(U).
+ * Alg. 10.4), applied as (D + L') D^-1 (D + U') with D = diag(U). A 5-point
+ * matrix stored as a 9-point one with zero corner entries gets its ILU(1)
+ * this way: in natural order its level-1 fill is exactly the (x+1, y-1) and
+ * (x-1, y+1) positions, and the other corners never fill.
  * Errors: NDIAG_EBREAKDOWN on a zero pivot (reported at the next sync).
  */
 ndiag_status ilu0_factor(ndiag* h, int mode);
