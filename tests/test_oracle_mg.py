@@ -228,6 +228,28 @@ def _pin_two_level(Mm):
     return len(H.levels) == 2 and np.allclose(got, want, rtol=0, atol=1e-10 * np.abs(want).max())
 
 
+def _pin_galerkin3(Mm):
+    n = (5, 4, 3)
+    g = np.random.default_rng(53)
+    N = int(np.prod(n))
+    d = -g.uniform(0.2, 1.0, size=(7, N))
+    d = W._zero_outside(d, n, 7)
+    d[0] = -d[1:].sum(axis=0) + g.uniform(0.05, 0.5, size=N)
+    nx, ny, nz = n
+    nc = [(v + 1) // 2 for v in n]
+    P = np.zeros((N, nc[0] * nc[1] * nc[2]))
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                P[(z * ny + y) * nx + x, ((z // 2) * nc[1] + y // 2) * nc[0] + x // 2] = 1.0
+    try:
+        dc = Mm.galerkin3(n, d)
+    except (ValueError, IndexError):
+        return False
+    A = assemble(n, 7, d).toarray()
+    return np.allclose(assemble(tuple(nc), 7, dc).toarray(), P.T @ A @ P, rtol=0, atol=1e-13)
+
+
 MUTANTS = [
     ("        return z + self.smooth(k, r - pb.matvec(z))", "        return z"),
     ("P.T @ (r - pb.matvec(z))", "P.T @ (r + pb.matvec(z))"),
@@ -237,11 +259,14 @@ MUTANTS = [
     ("            for _ in range(KC - 1):", "            for _ in range(KC):"),
     ("((0, 0), (-1, 0), (1, 0), (0, -1), (0, 1))", "((0, 0), (1, 0), (-1, 0), (0, -1), (0, 1))"),
     ("        z = self.smooth(k, r)\n", "        z = 0.0 * r\n"),
+    ("    I = ((z // 2) * nyc + y // 2) * nxc + x // 2", "    I = ((y // 2) * nzc + z // 2) * nxc + x // 2"),
+    ("_OFF7 = ((0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1))",
+     "_OFF7 = ((0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, 1), (0, 0, -1))"),
 ]
 
 
 def test_pins_hold_on_the_oracle():
-    assert _pin_galerkin(M) and _pin_coarsest(M) and _pin_two_level(M)
+    assert _pin_galerkin(M) and _pin_coarsest(M) and _pin_two_level(M) and _pin_galerkin3(M)
 
 
 @pytest.mark.parametrize("anchor,replacement", MUTANTS)
@@ -250,7 +275,7 @@ def test_pins_catch_planted_mistake(anchor, replacement):
     assert src.count(anchor) == 1, anchor
     mod = types.ModuleType("mg_mutant")
     exec(compile(src.replace(anchor, replacement), "mg_mutant", "exec"), mod.__dict__)
-    assert not (_pin_galerkin(mod) and _pin_coarsest(mod) and _pin_two_level(mod))
+    assert not (_pin_galerkin(mod) and _pin_coarsest(mod) and _pin_two_level(mod) and _pin_galerkin3(mod))
 
 
 # --- 3D 7-point cycle ------------------------------------------------------------
