@@ -256,6 +256,8 @@ ndiag_status ilu0_apply(ndiag* h, const void* r, void* z);
  *   r, z   DEVICE vectors (handle precision); z may alias r.
  *   Set-up: the first call on a device looks up the array's device address
  *   with that device current; make that first call before any stream capture.
+ *   Later calls look the address up again whenever the handle's stream is not
+ *   capturing, so a device reset between calls is picked up.
  *   Sharing: every call uses the same array and leaves its contents behind
  *   (the hand-off words are cleared by each call before use). Calls that
  *   overlap on the GPU (other streams, threads or handles) race on it.
@@ -301,7 +303,8 @@ typedef struct {
  * Stop rule: the recurrence residual meets rtol, then the true fp64 residual is
  * checked; if it is above rtol the method restarts from it. With precision
  * FP32/FP32_D16 the solve is an fp64 iterative refinement around fp32 inner
- * solves (inner tolerance 1e-5 relative).
+ * solves; each inner solve aims at the outer tolerance in one go, relative
+ * 0.5 rtol ||b|| / ||r|| clamped to [1e-6, 1e-3], at most 60 outer steps.
  * Errors: NDIAG_ENOCONV (maxit), NDIAG_EBREAKDOWN, NDIAG_ESTATE (ILU0 not factored).
  */
 ndiag_status krylov_solve(ndiag* h, int method, int precond, int mode, const double* omega,

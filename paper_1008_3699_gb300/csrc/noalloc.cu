@@ -29,14 +29,21 @@ std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
 // Device address of g_scratch on the current device. The host-side name of a
-// __device__ array is only a stand-in, so the address is looked up once per
-// device, with that device current.
-ndiag_status scratch_address(void** out) {
+// __device__ array is only a stand-in, so the address is looked up with that
+// device current. It is looked up again on every call made while `stream` is
+// not capturing (so a device reset, which may move the array, is picked up);
+// while it is capturing, the address found by the last such call is used.
+ndiag_status scratch_address(cudaStream_t stream, void** out) {
   int dev = -1;
   ND_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return NDIAG_EINVAL;
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("ilu0_apply_noalloc: device ordinal out of range");
+    return NDIAG_EINVAL;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  ND_CUDA(cudaStreamIsCapturing(stream, &cap));
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone || !g_addr[dev]) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess || !p) return cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
@@ -61,7 +68,7 @@ extern "C" ndiag_status ilu0_apply_noalloc(ndiag* h, const void* r, void* z) {
     return NDIAG_EINVAL;
   }
   void* base = nullptr;
-  ND_TRY(scratch_address(&base));
+  ND_TRY(scratch_address(h->stream, &base));
   unsigned char* b = static_cast<unsigned char*>(base);
   void* y = b;
   unsigned* sync = reinterpret_cast<unsigned*>(b + kVecBytes);

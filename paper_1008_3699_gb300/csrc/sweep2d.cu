@@ -474,7 +474,10 @@ ndiag_status tri_sweep_in_scratch(Handle* h, int kind, int mode, int64_t t, cons
   const unsigned nslabs = (unsigned)(px * py * P.spp);
   if (P.use_ticket) {
     const size_t need = sizeof(unsigned) * (1 + (size_t)nslabs);
-    if (need > sync_bytes || sizeof(T) * (size_t)nslabs > twin_bytes) return NDIAG_EINVAL;
+    if (need > sync_bytes || sizeof(T) * (size_t)nslabs > twin_bytes) {
+      set_error("ilu0_apply_noalloc: the subdomain split needs more than 64 Ki hand-off words");
+      return NDIAG_EINVAL;
+    }
     ND_CUDA(cudaMemsetAsync(sync, 0, need, h->stream));  // hand-off words start at zero
     P.ticket = sync;
     P.flags = sync + 1;
