@@ -55,6 +55,8 @@ def _load(path: str):
     lib.orc_fwd_phase.restype = I
     lib.orc_fwd_phase.argtypes = [I]
     lib.orc_solve.argtypes = [P, I, I, I, P, D, I, P, P, P]
+    lib.orc_history.argtypes = [P, P, L]
+    lib.orc_history.restype = L
     lib.orc_eik_create.restype = P
     lib.orc_eik_create.argtypes = [P, D, P, P]
     lib.orc_eik_destroy.argtypes = [P]
@@ -176,7 +178,15 @@ class Problem:
                                 _ptr(b), _ptr(x), _ptr(info))
         if rc:
             raise RuntimeError(f"oracle solve failed ({rc})")
-        return x, dict(iters=int(info[0]), relres=float(info[1]), status=int(info[2]))
+        out = dict(iters=int(info[0]), relres=float(info[1]), status=int(info[2]))
+        # per-iteration record (BiCGSTAB: ||s||/||b||, ||r||/||b||, alpha, omega;
+        # PCG: ||r||/||b||, alpha, 0, 0)
+        rows = self.lib.orc_history(self.h, None, 0)
+        hist = np.zeros((rows, 4))
+        if rows:
+            self.lib.orc_history(self.h, _ptr(hist), rows)
+        out["history"] = hist
+        return x, out
 
 
 class Eikonal:

@@ -197,6 +197,9 @@ struct Problem {
   int ilu_mode = -1;
   std::vector<double> dtilde;    // decomposed ILU(0) pivots
   std::vector<double> lu;        // natural ILU(0): s x N, L multipliers / U
+  // per-iteration record of the last Krylov solve, 4 values per iteration:
+  // BiCGSTAB ||s||/||b||, ||r||/||b||, alpha, omega; PCG ||r||/||b||, alpha, 0, 0
+  std::vector<double> hist;
 };
 
 inline double aval(const Problem& pb, int k, int64_t i) { return pb.A[(size_t)k * pb.g.N + i]; }
@@ -660,7 +663,9 @@ int pcg(Problem& pb, int prec, int mode, double omega, double rtol, int maxit, c
       for (int64_t i = 0; i < N; ++i) x[i] += alpha * p[i];
       for (int64_t i = 0; i < N; ++i) r[i] -= alpha * Ap[i];
       ++it;
-      if (std::sqrt(dot(N, r.data(), r.data())) / bnorm <= rtol) { recheck = true; break; }
+      const double rrel = std::sqrt(dot(N, r.data(), r.data())) / bnorm;
+      pb.hist.insert(pb.hist.end(), {rrel, alpha, 0.0, 0.0});
+      if (rrel <= rtol) { recheck = true; break; }
       if (!precond(pb, prec, mode, omega, r.data(), z.data())) return 3;
       const double rz2 = dot(N, r.data(), z.data());
       const double beta = rz2 / rz;
@@ -708,8 +713,10 @@ int bicgstab(Problem& pb, int prec, int mode, double omega, double rtol, int max
       alpha = rho / rv;
       for (int64_t i = 0; i < N; ++i) s[i] = r[i] - alpha * v[i];
       ++it;
-      if (std::sqrt(dot(N, s.data(), s.data())) / bnorm <= rtol) {
+      const double srel = std::sqrt(dot(N, s.data(), s.data())) / bnorm;
+      if (srel <= rtol) {  // the half step meets the tolerance: x += alpha ph, r = s
         for (int64_t i = 0; i < N; ++i) x[i] += alpha * ph[i];
+        pb.hist.insert(pb.hist.end(), {srel, srel, alpha, 0.0});
         recheck = true;
         break;
       }
@@ -719,7 +726,9 @@ int bicgstab(Problem& pb, int prec, int mode, double omega, double rtol, int max
       om = (tt == 0.0) ? 0.0 : dot(N, t.data(), s.data()) / tt;
       for (int64_t i = 0; i < N; ++i) x[i] += alpha * ph[i] + om * sh[i];
       for (int64_t i = 0; i < N; ++i) r[i] = s[i] - om * t[i];
-      if (std::sqrt(dot(N, r.data(), r.data())) / bnorm <= rtol) { recheck = true; break; }
+      const double rrel = std::sqrt(dot(N, r.data(), r.data())) / bnorm;
+      pb.hist.insert(pb.hist.end(), {srel, rrel, alpha, om});
+      if (rrel <= rtol) { recheck = true; break; }
     }
     if (!recheck) { info[0] = it; info[1] = true_relres(pb, b, x, bnorm, tmp); info[2] = 1; return 0; }
     const double tr = true_relres(pb, b, x, bnorm, tmp);
@@ -945,6 +954,7 @@ int orc_eik_solve(void* e, double* u, double delta, int max_rounds, double* info
 int orc_solve(void* h, int method, int prec, int mode, const double* omega, double rtol,
               int maxit, const double* b, double* x, double* info) {
   Problem& pb = *static_cast<Problem*>(h);
+  pb.hist.clear();
   if (prec == PREC_ILU0 && pb.ilu_mode != mode)
     if (!ilu0_factor(pb, mode)) return 4;
   switch (method) {
@@ -953,6 +963,16 @@ int orc_solve(void* h, int method, int prec, int mode, const double* omega, doub
     case METHOD_STATIONARY: return stationary(pb, mode, omega, rtol, maxit, b, x, info);
   }
   return 5;
+}
+
+// Rows (4 values each) of the last solve's per-iteration record copied to out,
+// at most cap; returns the number of rows the solve recorded.
+int64_t orc_history(void* h, double* out, int64_t cap) {
+  const Problem& pb = *static_cast<Problem*>(h);
+  const int64_t rows = (int64_t)pb.hist.size() / 4;
+  const int64_t n = std::min(rows, cap);
+  if (out && n > 0) std::memcpy(out, pb.hist.data(), sizeof(double) * 4 * (size_t)n);
+  return rows;
 }
 
 }  // extern "C"

@@ -7,6 +7,7 @@ Nothing here touches the CUDA library. Usage:
     python tests/golden/make_golden.py varcoef2048_envelope  # long: 7 perturbed solves in parallel
     python tests/golden/make_golden.py varcoef2048_mg  # long: one 2048^2 multigrid-PCG solve
     python tests/golden/make_golden.py poisson3d256_mg  # long: one 256^3 multigrid-PCG solve (about 10 GB)
+    python tests/golden/make_golden.py varcoef2048_history  # minutes: 40 BiCGSTAB iterations, 5 b's, 2 orders
 Output: tests/golden/<name>.json
 """
 import json
@@ -99,8 +100,53 @@ def varcoef2048_envelope(count=7):
     return dict(perturbation="b * (1 + 1e-15 g), g ~ N(0,1), seeds 4242..", runs=runs, min=min(its), max=max(its))
 
 
+HIST_ITERS, HIST_SEEDS = 40, 4
+
+
+def _history_run(args):
+    """First HIST_ITERS rows of the oracle's BiCGSTAB + ILU(0) record on the
+    2048^2 workload (mode: 1 decomposed 16 x 16, 0 natural), with b scaled by
+    (1 + 1e-15 g), g ~ N(0, 1) from seed 5151 + k, or unperturbed for k < 0."""
+    mode, k, n, sub = args
+    import oracle as orc
+    p = W.varcoef2d_problem(n, sub)
+    b = p["b"]
+    if k >= 0:
+        g = np.random.default_rng(5151 + k)
+        b = b * (1.0 + 1e-15 * g.standard_normal(b.shape[0]))
+    pb = orc.Problem(2, p["n"], 5, p["diags"], p["sub"] if mode else (1, 1))
+    pb.ilu0_factor(mode)
+    _, info = pb.solve(orc.BICGSTAB, orc.PREC_ILU0, mode, 1.0, 1e-8, HIST_ITERS, b)
+    return mode, k, info["history"].tolist()
+
+
+def varcoef2048_history(n=2048, sub=16):
+    """The oracle's BiCGSTAB + ILU(0) iteration record (||s||/||b||, ||r||/||b||,
+    alpha, omega) over the first HIST_ITERS iterations, decomposed and natural,
+    and its own spread under rounding-level changes of b: dev[k] = the largest
+    relative change of any of the four values at iteration k over HIST_SEEDS
+    perturbed right-hand sides (one process per solve, spawned)."""
+    import multiprocessing as mp
+    jobs = [(m, k, n, sub) for m in (1, 0) for k in range(-1, HIST_SEEDS)]
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+        runs = pool.map(_history_run, jobs)
+    out = dict(iters=HIST_ITERS, seeds=HIST_SEEDS, perturbation="b * (1 + 1e-15 g), g ~ N(0,1), seeds 5151..")
+    for m, name in ((1, "decomposed"), (0, "natural")):
+        base = np.array(next(h for mm, k, h in runs if mm == m and k < 0))
+        dev = np.zeros(len(base))
+        for mm, k, h in runs:
+            if mm != m or k < 0:
+                continue
+            h = np.array(h)
+            r = min(len(h), len(base))
+            dev[:r] = np.maximum(dev[:r], np.max(np.abs(h[:r] - base[:r]) / np.abs(base[:r]), axis=1))
+        out[name] = dict(history=base.tolist(), dev=dev.tolist())
+    return out
+
+
 JOBS = {"poisson64": poisson64, "varcoef2048": varcoef2048, "varcoef2048_envelope": varcoef2048_envelope,
-        "varcoef2048_mg": varcoef2048_mg, "poisson3d256_mg": poisson3d256_mg}
+        "varcoef2048_mg": varcoef2048_mg, "poisson3d256_mg": poisson3d256_mg,
+        "varcoef2048_history": varcoef2048_history}
 
 if __name__ == "__main__":
     oracle.build()
