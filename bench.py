@@ -126,7 +126,7 @@ def cpu_baseline(problem, iters=6):
     sweeps = 1 + 4 * info["iters"]  # factor + two applies (two sweeps each) per iteration
     return {"value": N * sweeps / dt / 1e9, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
             "sample": f"ILU(0) factor + {info['iters']} BiCGSTAB iterations of the 2048^2 workload "
-                      f"({sweeps} sweeps, {dt:.1f} s, 1 thread)"}
+                      f"({sweeps} sweeps, {dt:.1f} s, 1 thread)", "seconds": dt}
 
 
 def over_ranks(ms, updates, dist, device):
@@ -162,8 +162,14 @@ def run_reference(args):
         "cpu_baseline": {"value": v, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
                          "sample": vals[0]["sample"]},
         "e2e": {"value": v, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "ms_per_step": 2 * 1e3 * N / (v * 1e9) if v else None,
+        # one step = the bounded sample above (factor + 2 iterations), timed on the host
+        "ms_per_step": 1e3 * statistics.median(x["seconds"] for x in vals),
     }))
+
+
+def progress(msg):
+    """Where the run is, on stderr (the JSON line is the only stdout output)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
 
 def main():
@@ -183,6 +189,10 @@ def main():
                     help="varcoef2048 is the benchmark; the others print one measurement line each")
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--n3d", type=int, default=256, help="side of the 3D Poisson workload (subdomains of 32^3)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave out the 256^3 fp32 + refinement and 512-problem batch sub-measurements")
+    ap.add_argument("--roofline-iters", type=int, default=200,
+                    help="BiCGSTAB iterations of the pass that times every sweep launch")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -225,7 +235,9 @@ def main():
         return
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        progress("oracle sample on the host")
         cpu = cpu_baseline(problem)  # host only, before the GPU work
+    progress("warm-up steps")
 
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -245,10 +257,11 @@ def main():
             uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
         except Exception:
             pass
+        progress("timed steps")
         clocks = Clocks(uuid)
         barrier()
         torch.cuda.synchronize()
-        h.profile(True)
+        h.profile(False)  # counters only: the iteration runs as captured graphs
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         ev[0].record(stream)
         infos = []
@@ -264,6 +277,22 @@ def main():
                                            "cuda")
         value = all_updates / (total_ms / 1e3) / 1e9
 
+        progress("roofline pass")
+        # roofline pass: a bounded solve of the same system with every sweep
+        # launch timed by CUDA events on the handle's stream (the iteration is
+        # then launched kernel by kernel, not as graphs)
+        h.profile(True)
+        x.zero_()
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        h.solve(nd.BICGSTAB, nd.PREC_ILU0, b, x, rtol=1e-8, maxit=args.roofline_iters, raise_on_noconv=False)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        pc = h.counters()
+        pass_ms = r0.elapsed_time(r1)
+        h.profile(False)
+
+        progress("end-to-end steps")
         # end to end through the C ABI with pinned host buffers
         hb = torch.empty(N, dtype=torch.float64, pin_memory=True)
         hb.copy_(torch.from_numpy(problem["b"]))
@@ -292,6 +321,7 @@ def main():
 
         natural = None
         if not args.no_natural and rank == 0:
+            progress("natural-order comparison")
             hn = nd.NDiag(2, problem["n"], 5, problem["diags"], (1, 1), "fp64", stream=stream)
             hn.ilu0_factor(nd.NATURAL)
             xn = torch.zeros(N, dtype=torch.float64, device="cuda")
@@ -303,10 +333,24 @@ def main():
             natural = {"iters": ni["iters"], "relres": ni["relres"], "seconds": time.perf_counter() - t0}
             hn.close()
 
+        extras = None
+        if not args.no_extras and rank == 0:
+            progress("256^3 fp32 + refinement")
+            e3 = extra_fp32_refine_3d(torch, nd, W, args, 256)
+            progress("512-problem batch")
+            extras = {"fp32_refine_256cube": e3, "batch512": extra_batch512(torch, nd, W, args)}
+
     if rank != 0:
         return
     peak, peak_kind = measured_peaks()
-    achieved = cnt["sweep_bytes"] / (cnt["sweep_ms"] / 1e3) / 1e9 if cnt["sweep_ms"] > 0 else None
+    # algorithmic bytes of an fp64 ILU(0) apply: 80 B a cell (forward: two L
+    # entries, the pivot, r, y; backward: two U entries, the pivot, y, z), i.e.
+    # 40 B a cell for each of its two sweeps; the kernels' own count is 32 B (the
+    # unit form; the pivot scaling is read by the vector kernels instead)
+    B8D = 40.0
+    sweep_s = pc["sweep_ms"] / 1e3
+    achieved = B8D * N * pc["sweep_launches"] / sweep_s / 1e9 if sweep_s > 0 else None
+    achieved_kernel = pc["sweep_bytes"] / sweep_s / 1e9 if sweep_s > 0 else None
     lat_sorted = sorted(lat)
     p = lambda q: lat_sorted[min(len(lat_sorted) - 1, int(round(q * (len(lat_sorted) - 1))))]
     line = {
@@ -331,10 +375,16 @@ def main():
         "relres": max(i["relres"] for i in infos),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": kernel_traffic(),
-                     "kernel": "sweep2d_staged_kernel (ILU(0) apply sweeps; factor sweep in sweep2d_kernel)",
-                     "peak_kind": peak_kind, "sweep_launches": cnt["sweep_launches"],
-                     "sweep_ms": cnt["sweep_ms"], "sweep_bytes": cnt["sweep_bytes"]},
-        "sweep_share_of_step": cnt["sweep_ms"] / total_ms if total_ms else None,
+                     "bytes_per_cell": B8D,
+                     "bytes_basis": "algorithmic bytes of an fp64 ILU(0) apply, 80 B a cell = 2 sweeps x 40",
+                     "kernel": "sweep2d_staged_kernel (the two sweeps of every ILU(0) apply)",
+                     "peak_kind": peak_kind, "sweep_launches": pc["sweep_launches"], "sweep_ms": pc["sweep_ms"],
+                     "avg_launch_us": 1e3 * pc["sweep_ms"] / pc["sweep_launches"] if pc["sweep_launches"] else None,
+                     "timed_pass": f"{args.roofline_iters} BiCGSTAB iterations of the same system, "
+                                   "every sweep launch bracketed by CUDA events on the handle's stream",
+                     "kernel_counted": {"bytes_per_cell": 32.0, "achieved": achieved_kernel,
+                                        "frac": (achieved_kernel / peak) if achieved_kernel else None}},
+        "sweep_share_of_step": pc["sweep_ms"] / pass_ms if pass_ms else None,
         "gpu_launches": cnt["launches"],
         "e2e": {"value": float(e2e_val.item()), "unit": "Gcell-updates/s",
                 "h2d_bytes_per_step": int(hd_np.nbytes + hb_np.nbytes + hx_np.nbytes),
@@ -343,7 +393,111 @@ def main():
         "cpu_baseline": cpu,
         "natural_ilu0": natural,
     }
+    if extras:
+        line.update(extras)
     print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# Sub-measurements carried in the benchmark line: the 256^3 fp32 + refinement
+# solve and the 512-problem batch.
+# ---------------------------------------------------------------------------
+
+def extra_fp32_refine_3d(torch, nd, W, args, n):
+    """n^3 Poisson, 32^3 subdomains: fp32 SSOR-PCG with fp64 residuals and
+    refinement to rel-res 1e-8 (one warm-up solve, one timed), the fp32 SSOR
+    apply timed with CUDA events, and the oracle's fp64 SSOR apply on a 128^3
+    sample of the same problem family on one host core."""
+    p = W.poisson3d_problem(n, max(1, n // 32))
+    N = n ** 3
+    h = nd.NDiag(3, p["n"], 7, p["diags"], p["sub"], "fp32")
+    b = torch.tensor(p["b"], device="cuda")
+    for _ in range(2):
+        x = torch.zeros_like(b)
+        info = _timed_solve(torch, h, nd.PCG, nd.PREC_SSOR, b, x, rtol=1e-8, maxit=5000)
+    r = b.float()
+    z = torch.empty_like(r)
+    for _ in range(2):
+        h.ssor_apply(1.0, r, z)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(5):
+        h.ssor_apply(1.0, r, z)
+    e1.record()
+    torch.cuda.synchronize()
+    apply_ms = e0.elapsed_time(e1) / 5
+    h.close()
+    # algorithmic bytes of an fp32 7-point SSOR apply: forward (pivot, 3
+    # entries, r, tmp) and transposed solve (3 entries, tmp, z), 4 B each
+    bpc = 4.0 * ((4 + 2) + (3 + 2))
+    peak, kind = measured_peaks()
+    gbs = bpc * N / (apply_ms / 1e3) / 1e9
+    out = {"workload": f"poisson3d-{n}^3-7pt-fp32-ssor-pcg+fp64-refinement-{max(1, n // 32)}^3",
+           "seconds": info["wall_s"], "solves_per_s": 1.0 / info["wall_s"], "iters": info["iters"],
+           "outer": info["outer"], "relres": info["relres"], "ssor_apply_ms": apply_ms,
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                        "bytes_per_cell": bpc, "peak_kind": kind,
+                        "kernel": "fp32 SSOR apply (sweep3d block passes + pencil passes)"}}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        ns = 128
+        q = W.poisson3d_problem(ns, ns // 32)
+        pb = oracle.Problem(3, q["n"], 7, q["diags"], q["sub"])
+        pb.ssor_apply(oracle.DECOMPOSED, 1.0, q["b"])  # builds the sweep plan
+        t0 = time.perf_counter()
+        pb.ssor_apply(oracle.DECOMPOSED, 1.0, q["b"])
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": 2 * ns ** 3 / dt / 1e9, "unit": "Gcell-updates/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"one fp64 SSOR apply (two sweeps) of the oracle at {ns}^3, 32^3 "
+                                         f"subdomains ({dt:.2f} s)"}
+    return out
+
+
+def extra_batch512(torch, nd, W, args):
+    """512 problems (sides U[32,512], log-uniform coefficients): the batched
+    fp32 + fp64-refinement SSOR-PCG (autotuned tile, graph-captured chunks),
+    beside fp64 SSOR-PCG with one handle per problem on the first 64 problems,
+    and the oracle on the first 4 problems (one host core)."""
+    import numpy as np
+    probs = W.batched_problems(512, 32, 512, 1004)
+    b = torch.tensor(np.concatenate([q["b"] for q in probs]), device="cuda")
+    B = nd.Batch(probs, tile=64)
+    B.autotune(b)
+    for _ in range(2):
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = B.solve(b, x, rtol=1e-8)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    out = {"workload": "batch-512x2d-5pt-U[32,512]-fp32+fp64ref-ssor-pcg", "solves_per_s": len(probs) / dt,
+           "seconds": dt, "tile": int(B.tiles()[0]), "relres_max": max(i["relres"] for i in infos),
+           "iters_mean": float(np.mean([i["iters"] for i in infos])), "launches": B.launches()}
+    B.close()
+    tot = 0.0
+    for q in probs[:64]:
+        sub = (max(1, -(-q["n"][0] // 64)), max(1, -(-q["n"][1] // 64)))
+        h = nd.NDiag(2, q["n"], 5, q["diags"], sub, "fp64")
+        bk = torch.tensor(q["b"], device="cuda")
+        tot += _timed_solve(torch, h, nd.PCG, nd.PREC_SSOR, bk, torch.zeros_like(bk), rtol=1e-8,
+                            maxit=20000)["wall_s"]
+        h.close()
+    out["fp64_one_per_handle"] = {"solves_per_s": 64 / tot, "sample": "the first 64 problems, one solve each"}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        for q in probs[:4]:
+            sub = (max(1, -(-q["n"][0] // 64)), max(1, -(-q["n"][1] // 64)))
+            pb = oracle.Problem(2, q["n"], 5, q["diags"], sub)
+            pb.solve(oracle.PCG, oracle.PREC_SSOR, oracle.DECOMPOSED, 1.0, 1e-8, 20000, q["b"])
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": 4 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                               "sample": f"fp64 SSOR-PCG of the first 4 problems ({dt:.1f} s)"}
+    return out
 
 
 # ---------------------------------------------------------------------------

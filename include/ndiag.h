@@ -301,7 +301,12 @@ typedef struct {
  *   b, x    fp64 vectors, DEVICE or HOST pointers (detected); x holds the
  *           initial guess and receives the solution.
  * Stop rule: the recurrence residual meets rtol, then the true fp64 residual is
- * checked; if it is above rtol the method restarts from it. With precision
+ * checked; if it is above rtol the method restarts from it. PCG and BiCGSTAB
+ * make their stop tests on the device and the host reads the scalars once per
+ * chunk of 8 iterations; after the first chunk each chunk is replayed as one
+ * captured CUDA graph (not while ndiag_profile is on, and not with the
+ * multigrid preconditioner). Iterations the device enqueues after it stopped
+ * leave x unchanged. With precision
  * FP32/FP32_D16 the solve is an fp64 iterative refinement around fp32 inner
  * solves; each inner solve aims at the outer tolerance in one go, relative
  * 0.5 rtol ||b|| / ||r|| clamped to [1e-6, 1e-3], at most 60 outer steps.
@@ -310,6 +315,27 @@ typedef struct {
 ndiag_status krylov_solve(ndiag* h, int method, int precond, int mode, const double* omega,
                           double rtol, int maxit, const double* b, double* x,
                           ndiag_solve_info* info);
+
+/*
+ * ndiag_set_history -- record every iteration of the following krylov_solve
+ * calls on this handle, so that a solve can be compared with another
+ * implementation of the same method iteration by iteration (the residual
+ * history before rounding differences grow, Sec. 5 for the preconditioner).
+ *   out       HOST array of 4 * capacity doubles, owned by the caller; it must
+ *             stay valid until the last solve that records into it returns.
+ *             Row k (iteration k + 1) holds, for BiCGSTAB: ||s_k|| / ||b||,
+ *             ||r_k|| / ||b||, alpha_k, omega_k (the recurrence vectors of the
+ *             two half steps; omega_k = 0 when the half step met the
+ *             tolerance); for PCG: ||r_k|| / ||b||, alpha_k, 0, 0. Rows are
+ *             written for min(iterations, capacity) iterations, when the solve
+ *             returns.
+ *   capacity  rows of out; 0 or out = NULL stops recording.
+ * Only FP64 handles record (the fp32 inner solves of the refinement do not);
+ * the stationary method records nothing. The library allocates a device copy
+ * of 32 * capacity bytes, freed by the next call or by ndiag_destroy.
+ * Errors: NDIAG_EINVAL (capacity < 0), NDIAG_ENOMEM.
+ */
+ndiag_status ndiag_set_history(ndiag* h, double* out, int capacity);
 
 /*
  * ndiag_tune_omega -- a relaxation factor per sweep direction for the

@@ -386,6 +386,7 @@ void ndiag_destroy(ndiag* h) {
   dev_free(h->kws.p, h->kws.bytes, s);
   dev_free(h->red, h->red_bytes, s);
   dev_free(h->tmp, h->tmp_bytes, s);
+  dev_free(h->hist_dev, sizeof(double) * 4 * (size_t)h->hist_cap, s);
   cudaStreamSynchronize(s);
   for (ProfRec& r : h->prof) {
     cudaEventDestroy(r.a);

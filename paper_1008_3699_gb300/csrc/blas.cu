@@ -266,6 +266,7 @@ template <class T>
 __global__ void __launch_bounds__(BT, BPS) bicg_p_kernel(int64_t N, const T* __restrict__ r, T* __restrict__ p,
                                                          const T* __restrict__ v, const double* sc, int first,
                                                          const T* __restrict__ inv, T* __restrict__ sp) {
+  if (sc[SC_DONE] != 0.0) return;  // the iteration has stopped
   const double rho = sc[SC_RHO], rho_old = sc[SC_RHO_OLD], alpha = sc[SC_ALPHA], om = sc[SC_OM];
   const double beta = first ? 0.0 : (rho / rho_old) * (alpha / om);
   constexpr int U = 4;  // three or four streams in
@@ -302,6 +303,7 @@ __global__ void __launch_bounds__(BT, BPS) bicg_s_kernel(int64_t N, const T* __r
                                                          const T* __restrict__ v, T* __restrict__ s,
                                                          const double* sc, Reduce R, const T* __restrict__ inv,
                                                          T* __restrict__ ss) {
+  if (sc[SC_DONE] != 0.0) return;  // every block returns: the reduction is not touched
   const double alpha = sc[SC_RHO] / sc[SC_RV];
   double d = 0.0;
   constexpr int U = 4;  // two or three streams in
@@ -342,6 +344,7 @@ __global__ void __launch_bounds__(BT, BPS) bicg_xr_kernel(int64_t N, T* __restri
   // leaves x and r as they are; the host reports it. A first half step that
   // already meets the tolerance (||s||^2 <= tol^2) takes om = 0: x += alpha ph
   // and r = s, the solution of the half step.
+  if (sc[SC_DONE] != 0.0) return;
   const double rho = sc[SC_RHO], rv = sc[SC_RV], ss = sc[SC_SS];
   if (rho == 0.0 || rv == 0.0 || !isfinite(ss)) return;
   const double alpha = rho / rv;
@@ -397,6 +400,7 @@ template <class T>
 __global__ void __launch_bounds__(BT, BPS) cg_xr_kernel(int64_t N, T* __restrict__ x, const T* __restrict__ p,
                                                         T* __restrict__ r, const T* __restrict__ q,
                                                         const double* sc, Reduce R) {
+  if (sc[SC_DONE] != 0.0) return;
   const double alpha = sc[SC_RZ] / sc[SC_PQ];
   double d = 0.0;
   constexpr int U = 4;  // four streams
@@ -425,6 +429,7 @@ __global__ void __launch_bounds__(BT, BPS) cg_xr_kernel(int64_t N, T* __restrict
 template <class T>
 __global__ void __launch_bounds__(BT, BPS) cg_p_kernel(int64_t N, const T* __restrict__ z, T* __restrict__ p,
                                                        const double* sc, int first) {
+  if (sc[SC_DONE] != 0.0) return;
   const double beta = first ? 0.0 : sc[SC_RZ_NEW] / sc[SC_RZ];
   constexpr int U = 8;  // two streams in
   ND_STREAM_LOOP(N) {
@@ -445,7 +450,9 @@ __global__ void __launch_bounds__(BT, BPS) cg_p_kernel(int64_t N, const T* __res
   }
 }
 
-__global__ void copy_scalar_kernel(double* sc, int dst, int src) { sc[dst] = sc[src]; }
+__global__ void copy_scalar_kernel(double* sc, int dst, int src) {
+  if (sc[SC_DONE] == 0.0) sc[dst] = sc[src];
+}
 
 template <class TD, class TS>
 __global__ void __launch_bounds__(BT, BPS) convert_kernel(int64_t N, const TS* __restrict__ s, TD* __restrict__ d) {

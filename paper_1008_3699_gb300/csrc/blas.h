@@ -18,8 +18,14 @@ enum { RED_SLOTS = 4, RED_RES = 64 };
 enum {
   SC_BASE = 16,
   SC_RHO = SC_BASE, SC_RHO_OLD, SC_ALPHA, SC_OM, SC_RV, SC_TS, SC_TT, SC_SS, SC_RR, SC_RHO_NEXT,
-  SC_RZ, SC_RZ_NEW, SC_PQ, SC_BB, SC_R0, SC_TOL2, SC_END
+  SC_RZ, SC_RZ_NEW, SC_PQ, SC_BB, SC_R0, SC_TOL2,
+  // device-resident iteration: state word, iterations done, limit, tolerance
+  SC_DONE, SC_ITER, SC_MAXIT, SC_TOL, SC_END
 };
+// SC_DONE values: the iteration runs (0) or has stopped, and why. Once it is
+// non-zero the update kernels leave x, r, p and the scalars as they are.
+enum { DONE_RUN = 0, DONE_CONV = 1, DONE_BREAK = 2, DONE_BREAK_NONFINITE = 3, DONE_BREAK_OMEGA = 4,
+       DONE_MAXIT = 5 };
 
 int grid_blocks(const Handle* h);
 size_t reduce_bytes(const Handle* h);
@@ -46,6 +52,7 @@ template <class T> ndiag_status cg_xr(Handle* h, T* x, const T* p, T* r, const T
 template <class T> ndiag_status cg_p(Handle* h, const T* z, T* p, const double* sc, int first);
 template <class T> ndiag_status scale(Handle* h, T* x, double f);
 template <class T> ndiag_status mul_diag(Handle* h, const T* x, T* y);
+// sc[dst] = sc[src] unless the iteration has stopped (sc[SC_DONE] != 0)
 ndiag_status copy_scalar(Handle* h, double* sc, int dst, int src);
 ndiag_status to32(Handle* h, const double* s, float* d);
 ndiag_status add_to(Handle* h, double* x, const float* e);

@@ -125,6 +125,10 @@ struct Handle {
   double* red_host = nullptr;    // pinned mirror of the results
   void* tmp = nullptr;           // one vector in sweep precision (ssor/ilu intermediates)
   size_t tmp_bytes = 0;
+  // per-iteration record of the fp64 Krylov solves (ndiag_set_history)
+  double* hist_dev = nullptr;    // device, 4 values per iteration
+  int hist_cap = 0;              // iterations it holds
+  double* hist_user = nullptr;   // host buffer the caller gave
 
   // counters (ndiag_profile / ndiag_read_counters)
   int64_t launches = 0;

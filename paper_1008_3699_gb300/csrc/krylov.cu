@@ -21,6 +21,7 @@ ndiag_status check_device_status(Handle* h);
 namespace {
 
 __global__ void bicg_scalars_kernel(double* sc, int first) {
+  if (!first && sc[SC_DONE] != 0.0) return;  // stopped: keep the scalars
   if (first) {
     sc[SC_RHO_OLD] = 1.0;
     sc[SC_ALPHA] = 1.0;
@@ -31,6 +32,65 @@ __global__ void bicg_scalars_kernel(double* sc, int first) {
     sc[SC_OM] = sc[SC_TT] == 0.0 ? 0.0 : sc[SC_TS] / sc[SC_TT];
   }
   sc[SC_RHO] = sc[SC_RHO_NEXT];
+}
+
+// State of a device-resident iteration: running, iterations so far, limit,
+// tolerance (absolute ||r||) and its square.
+__global__ void loop_init_kernel(double* sc, double it, double maxit, double tol) {
+  sc[SC_DONE] = DONE_RUN;
+  sc[SC_ITER] = it;
+  sc[SC_MAXIT] = maxit;
+  sc[SC_TOL] = tol;
+  sc[SC_TOL2] = tol * tol;
+}
+
+// End of one BiCGSTAB iteration: the tests a host would make after reading the
+// scalars, in the same order, so the device decides when to stop. Records the
+// iteration (||s||^2, ||r||^2, alpha, omega) when a history buffer is given.
+__global__ void bicg_check_kernel(double* sc, double* hist, int cap) {
+  if (sc[SC_DONE] != 0.0) return;
+  const double rho = sc[SC_RHO], rv = sc[SC_RV], ss = sc[SC_SS], rr = sc[SC_RR];
+  const double ts = sc[SC_TS], tt = sc[SC_TT];
+  if (rho == 0.0 || rv == 0.0 || !isfinite(ss)) {  // breakdown of the first half step
+    sc[SC_DONE] = DONE_BREAK;
+    return;
+  }
+  const double it = sc[SC_ITER] + 1.0;
+  sc[SC_ITER] = it;
+  if (hist && it <= (double)cap) {
+    double* e = hist + 4 * ((int64_t)it - 1);
+    e[0] = ss;
+    e[1] = rr;
+    e[2] = rho / rv;
+    e[3] = (ss <= sc[SC_TOL2] || tt == 0.0) ? 0.0 : ts / tt;  // the omega bicg_xr used
+  }
+  if (ss <= sc[SC_TOL2]) sc[SC_DONE] = DONE_CONV;  // the half step met the tolerance
+  else if (!isfinite(rr)) sc[SC_DONE] = DONE_BREAK_NONFINITE;
+  else if (sqrt(rr) <= sc[SC_TOL]) sc[SC_DONE] = DONE_CONV;
+  else if (tt == 0.0 || ts == 0.0) sc[SC_DONE] = DONE_BREAK_OMEGA;
+  else if (it >= sc[SC_MAXIT]) sc[SC_DONE] = DONE_MAXIT;
+}
+
+// End of one PCG iteration (after x and r are updated): records
+// (||r||^2, alpha) and decides whether to stop.
+__global__ void cg_check_kernel(double* sc, double* hist, int cap) {
+  if (sc[SC_DONE] != 0.0) return;
+  const double pq = sc[SC_PQ], rz = sc[SC_RZ], rr = sc[SC_RR];
+  if (pq == 0.0 || rz == 0.0 || !isfinite(rr)) {
+    sc[SC_DONE] = DONE_BREAK;
+    return;
+  }
+  const double it = sc[SC_ITER] + 1.0;
+  sc[SC_ITER] = it;
+  if (hist && it <= (double)cap) {
+    double* e = hist + 4 * ((int64_t)it - 1);
+    e[0] = rr;
+    e[1] = rz / pq;
+    e[2] = 0.0;
+    e[3] = 0.0;
+  }
+  if (sqrt(rr) <= sc[SC_TOL]) sc[SC_DONE] = DONE_CONV;
+  else if (it >= sc[SC_MAXIT]) sc[SC_DONE] = DONE_MAXIT;
 }
 
 template <class T>
@@ -100,84 +160,182 @@ ndiag_status init_residual(Handle* h, const T* b, const T* x, T* r, double* rr_d
   return dots<T>(h, 1, r, r, nullptr, nullptr, nullptr, nullptr, rr_dev, 3);
 }
 
+ndiag_status loop_init(Handle* h, int it, int maxit, double tol) {
+  ++h->launches;
+  loop_init_kernel<<<1, 1, 0, h->stream>>>(h->red, (double)it, (double)maxit, tol);
+  ND_CUDA(cudaGetLastError());
+  return NDIAG_OK;
+}
+ndiag_status scalars(Handle* h, int first) {
+  ++h->launches;
+  bicg_scalars_kernel<<<1, 1, 0, h->stream>>>(h->red, first);
+  ND_CUDA(cudaGetLastError());
+  return NDIAG_OK;
+}
+
+constexpr int CHUNK = 8;  // iterations enqueued between two host reads of the scalars
+
+// Captures CHUNK calls of `body` into one executable graph. The launch counters
+// are left as they were and the chunk's counts returned. False if the stream
+// cannot be captured here (the caller then launches the chunk directly).
+template <class Body>
+bool capture_chunk(Handle* h, Body& body, cudaGraphExec_t* exec, int64_t* d_launch, int64_t* d_sweep,
+                   double* d_bytes) {
+  const int64_t l0 = h->launches, s0 = h->sweep_launches;
+  const double b0 = h->sweep_bytes;
+  *exec = nullptr;
+  if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  ndiag_status st = NDIAG_OK;
+  for (int k = 0; k < CHUNK && st == NDIAG_OK; ++k) st = body();
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  *d_launch = h->launches - l0;
+  *d_sweep = h->sweep_launches - s0;
+  *d_bytes = h->sweep_bytes - b0;
+  h->launches = l0;
+  h->sweep_launches = s0;
+  h->sweep_bytes = b0;
+  bool ok = st == NDIAG_OK && e == cudaSuccess && g != nullptr;
+  if (ok) ok = cudaGraphInstantiate(exec, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();
+    *exec = nullptr;
+  }
+  return ok;
+}
+
+// Runs `body` (the launches of one iteration) in chunks of CHUNK until the
+// device stops the iteration, reading the scalars once per chunk. The first
+// chunk is launched directly (it also creates every table and buffer that is
+// made on first use); with `graph`, the later chunks are one captured CUDA
+// graph, replayed. The graph lives for this call. Returns the stop code and
+// the iteration count the device reached.
+template <class Body>
+ndiag_status device_loop(Handle* h, bool graph, int max_iters, Body body, int* done, int* iters) {
+  cudaGraphExec_t exec = nullptr;
+  int64_t g_launch = 0, g_sweep = 0;
+  double g_bytes = 0.0;
+  bool first = true, tried = false;
+  ndiag_status st = NDIAG_OK;
+  // the device stops at the iteration limit at the latest; a chunk more than
+  // that means its state word was never set
+  const int64_t max_chunks = (int64_t)std::max(max_iters, 0) / CHUNK + 2;
+  for (int64_t chunk = 0;; ++chunk) {
+    if (chunk > max_chunks) {
+      set_error("Krylov iteration: the device did not report a stop within the iteration limit");
+      st = NDIAG_EDEVICE;
+      break;
+    }
+    if (!first && graph && !tried) {
+      tried = true;
+      capture_chunk(h, body, &exec, &g_launch, &g_sweep, &g_bytes);
+    }
+    if (exec) {
+      if (cudaGraphLaunch(exec, h->stream) != cudaSuccess) {
+        st = cuda_status(cudaGetLastError(), "cudaGraphLaunch(Krylov chunk)");
+        break;
+      }
+      h->launches += g_launch;
+      h->sweep_launches += g_sweep;
+      h->sweep_bytes += g_bytes;
+    } else {
+      for (int k = 0; k < CHUNK && st == NDIAG_OK; ++k) st = body();
+      if (st != NDIAG_OK) break;
+    }
+    first = false;
+    st = pull(h);
+    if (st != NDIAG_OK) break;
+    const double d = h->red_host[SC_DONE];
+    if (d != 0.0) {
+      *done = (int)d;
+      *iters = (int)h->red_host[SC_ITER];
+      break;
+    }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  return st;
+}
+
+// Capture is left out while launches are being timed one by one, and for the
+// multigrid preconditioner, whose hierarchy is built on the host on first use.
+bool graph_allowed(const Handle* h, const Prec& P) { return !h->profiling && P.kind != NDIAG_PREC_MG; }
+
 // BiCGSTAB (van der Vorst 1992), right preconditioned. Stops when the
 // recurrence residual meets tol_abs; with `recheck`, then verifies the true
-// residual and restarts from it if it is above tol_abs.
+// residual and restarts from it if it is above tol_abs. The iteration runs on
+// the device: a check kernel at the end of every iteration makes the stop
+// tests (including the half-step exit, taken by bicg_xr with om = 0), and the
+// host reads the scalars once per chunk of iterations.
 template <class T>
 ndiag_status bicgstab(Handle* h, const Prec& P, const T* b, T* x, const KV<T>& V, double tol_abs, int maxit,
                       bool recheck, bool x_is_zero, int* iters) {
   double* sc = h->red;
   const double* hs = h->red_host;
   const size_t vb = sizeof(T) * (size_t)h->N;
+  // with the pre-scaled ILU(0) apply the vector kernels also write the
+  // pivot-scaled copies p / d~ and s / d~ its forward sweeps read
+  const bool pre = V.ps != nullptr;
+  const T* inv = pre ? (const T*)ilu_pivot_inverse(h) : nullptr;
+  double* hist = sizeof(T) == 8 ? h->hist_dev : nullptr;
+  const int cap = hist ? h->hist_cap : 0;
+  auto iteration = [&](int first) -> ndiag_status {
+    ND_TRY(bicg_p<T>(h, V.r, V.p, V.v, sc, first, inv, V.ps));
+    if (pre) ND_TRY(do_ilu_apply_pre(h, V.ps, V.ph));
+    else ND_TRY(apply_prec(h, P, V.p, V.ph, vb));
+    ND_TRY(spmv_dot<T>(h, V.ph, V.v, V.rh, sc + SC_RV, 1));
+    ND_TRY(bicg_s<T>(h, V.r, V.v, V.s, sc, inv, V.ss));
+    if (pre) ND_TRY(do_ilu_apply_pre(h, V.ss, V.sh));
+    else ND_TRY(apply_prec(h, P, V.s, V.sh, vb));
+    ND_TRY(spmv_dot<T>(h, V.sh, V.t, V.s, sc + SC_TS, 2, true));
+    ND_TRY(bicg_xr<T>(h, x, V.ph, V.sh, V.r, V.s, V.t, V.rh, sc));
+    ++h->launches;
+    bicg_check_kernel<<<1, 1, 0, h->stream>>>(sc, hist, cap);
+    ND_CUDA(cudaGetLastError());
+    return scalars(h, 0);  // the next iteration's alpha, omega, rho
+  };
   int it = 0;
-  h->red_host[SC_TOL2] = tol_abs * tol_abs;  // the device's half-step exit test
-  ND_CUDA(cudaMemcpyAsync(sc + SC_TOL2, h->red_host + SC_TOL2, sizeof(double), cudaMemcpyHostToDevice, h->stream));
   for (;;) {
     ND_TRY(init_residual<T>(h, b, x, V.r, sc + SC_R0, x_is_zero));
     ND_TRY(pull(h));
     if (std::sqrt(hs[SC_R0]) <= tol_abs) break;
-    ND_TRY(vcopy<T>(h, V.r, V.rh));
-    ND_TRY(dots<T>(h, 1, V.rh, V.r, nullptr, nullptr, nullptr, nullptr, sc + SC_RHO_NEXT, 1));
-    bool converged = false;
-    int first = 1;
-    // one host read per iteration: the half-step exit is taken on the device
-    // (bicg_xr with om = 0), and is recognised here from ||s||
-    while (it < maxit) {
-      ++h->launches;
-      bicg_scalars_kernel<<<1, 1, 0, h->stream>>>(sc, first);
-      ND_CUDA(cudaGetLastError());
-      // with the pre-scaled ILU(0) apply the vector kernels also write the
-      // pivot-scaled copies p / d~ and s / d~ its forward sweeps read
-      const bool pre = V.ps != nullptr;
-      const T* inv = pre ? (const T*)ilu_pivot_inverse(h) : nullptr;
-      ND_TRY(bicg_p<T>(h, V.r, V.p, V.v, sc, first, inv, V.ps));
-      first = 0;
-      if (pre) ND_TRY(do_ilu_apply_pre(h, V.ps, V.ph));
-      else ND_TRY(apply_prec(h, P, V.p, V.ph, vb));
-      ND_TRY(spmv_dot<T>(h, V.ph, V.v, V.rh, sc + SC_RV, 1));
-      ND_TRY(bicg_s<T>(h, V.r, V.v, V.s, sc, inv, V.ss));
-      if (pre) ND_TRY(do_ilu_apply_pre(h, V.ss, V.sh));
-      else ND_TRY(apply_prec(h, P, V.s, V.sh, vb));
-      ND_TRY(spmv_dot<T>(h, V.sh, V.t, V.s, sc + SC_TS, 2, true));
-      ND_TRY(bicg_xr<T>(h, x, V.ph, V.sh, V.r, V.s, V.t, V.rh, sc));
-      ND_TRY(pull(h));
-      if (hs[SC_RHO] == 0.0 || hs[SC_RV] == 0.0 || !std::isfinite(hs[SC_SS])) {
-        *iters = it;
-        set_error("BiCGSTAB breakdown");
-        return NDIAG_EBREAKDOWN;
-      }
-      ++it;
-      if (hs[SC_SS] <= hs[SC_TOL2]) {
-        converged = true;
-        break;
-      }
-      if (!std::isfinite(hs[SC_RR])) {
-        *iters = it;
-        set_error("BiCGSTAB breakdown (non-finite residual)");
-        return NDIAG_EBREAKDOWN;
-      }
-      if (std::sqrt(hs[SC_RR]) <= tol_abs) {
-        converged = true;
-        break;
-      }
-      if (hs[SC_TT] == 0.0 || hs[SC_TS] == 0.0) {
-        *iters = it;
-        set_error("BiCGSTAB breakdown (omega = 0)");
-        return NDIAG_EBREAKDOWN;
-      }
-    }
-    if (!converged) {
+    if (it >= maxit) {
       *iters = it;
       return NDIAG_ENOCONV;
     }
-    if (!recheck) break;
+    ND_TRY(vcopy<T>(h, V.r, V.rh));
+    ND_TRY(dots<T>(h, 1, V.rh, V.r, nullptr, nullptr, nullptr, nullptr, sc + SC_RHO_NEXT, 1));
+    ND_TRY(loop_init(h, it, maxit, tol_abs));
+    ND_TRY(scalars(h, 1));
+    ND_TRY(iteration(1));
+    int done = DONE_RUN;
+    ND_TRY(device_loop(h, graph_allowed(h, P), maxit - it, [&] { return iteration(0); }, &done, &it));
+    *iters = it;
+    if (done == DONE_MAXIT) return NDIAG_ENOCONV;
+    if (done == DONE_BREAK) {
+      set_error("BiCGSTAB breakdown");
+      return NDIAG_EBREAKDOWN;
+    }
+    if (done == DONE_BREAK_NONFINITE) {
+      set_error("BiCGSTAB breakdown (non-finite residual)");
+      return NDIAG_EBREAKDOWN;
+    }
+    if (done == DONE_BREAK_OMEGA) {
+      set_error("BiCGSTAB breakdown (omega = 0)");
+      return NDIAG_EBREAKDOWN;
+    }
+    if (!recheck) break;  // DONE_CONV
     x_is_zero = false;
   }
   *iters = it;
   return NDIAG_OK;
 }
 
-// Preconditioned CG (Saad Alg. 9.1), same stop rule.
+// Preconditioned CG (Saad Alg. 9.1), same stop rule, the same device-resident
+// loop.
 template <class T>
 ndiag_status pcg(Handle* h, const Prec& P, const T* b, T* x, const KV<T>& V, double tol_abs, int maxit,
                  bool recheck, bool x_is_zero, int* iters) {
@@ -185,37 +343,39 @@ ndiag_status pcg(Handle* h, const Prec& P, const T* b, T* x, const KV<T>& V, dou
   const double* hs = h->red_host;
   const size_t vb = sizeof(T) * (size_t)h->N;
   T *r = V.r, *z = V.s, *p = V.p, *q = V.v;
+  double* hist = sizeof(T) == 8 ? h->hist_dev : nullptr;
+  const int cap = hist ? h->hist_cap : 0;
+  auto iteration = [&]() -> ndiag_status {
+    ND_TRY(spmv_dot<T>(h, p, q, p, sc + SC_PQ, 2));
+    ND_TRY(cg_xr<T>(h, x, p, r, q, sc));
+    ++h->launches;
+    cg_check_kernel<<<1, 1, 0, h->stream>>>(sc, hist, cap);
+    ND_CUDA(cudaGetLastError());
+    ND_TRY(apply_prec(h, P, r, z, vb));
+    ND_TRY(dots<T>(h, 1, r, z, nullptr, nullptr, nullptr, nullptr, sc + SC_RZ_NEW, 1));
+    ND_TRY(cg_p<T>(h, z, p, sc, 0));
+    return copy_scalar(h, sc, SC_RZ, SC_RZ_NEW);
+  };
   int it = 0;
   for (;;) {
     ND_TRY(init_residual<T>(h, b, x, r, sc + SC_R0, x_is_zero));
     ND_TRY(pull(h));
     if (std::sqrt(hs[SC_R0]) <= tol_abs) break;
+    if (it >= maxit) {
+      *iters = it;
+      return NDIAG_ENOCONV;
+    }
+    ND_TRY(loop_init(h, it, maxit, tol_abs));  // before cg_p, which skips once stopped
     ND_TRY(apply_prec(h, P, r, z, vb));
     ND_TRY(dots<T>(h, 1, r, z, nullptr, nullptr, nullptr, nullptr, sc + SC_RZ, 1));
     ND_TRY(cg_p<T>(h, z, p, sc, 1));
-    bool converged = false;
-    while (it < maxit) {
-      ND_TRY(spmv_dot<T>(h, p, q, p, sc + SC_PQ, 2));
-      ND_TRY(cg_xr<T>(h, x, p, r, q, sc));
-      ND_TRY(pull(h));
-      if (hs[SC_PQ] == 0.0 || hs[SC_RZ] == 0.0 || !std::isfinite(hs[SC_RR])) {
-        *iters = it;
-        set_error("PCG breakdown");
-        return NDIAG_EBREAKDOWN;
-      }
-      ++it;
-      if (std::sqrt(hs[SC_RR]) <= tol_abs) {
-        converged = true;
-        break;
-      }
-      ND_TRY(apply_prec(h, P, r, z, vb));
-      ND_TRY(dots<T>(h, 1, r, z, nullptr, nullptr, nullptr, nullptr, sc + SC_RZ_NEW, 1));
-      ND_TRY(cg_p<T>(h, z, p, sc, 0));
-      ND_TRY(copy_scalar(h, sc, SC_RZ, SC_RZ_NEW));
-    }
-    if (!converged) {
-      *iters = it;
-      return NDIAG_ENOCONV;
+    int done = DONE_RUN;
+    ND_TRY(device_loop(h, graph_allowed(h, P), maxit - it, iteration, &done, &it));
+    *iters = it;
+    if (done == DONE_MAXIT) return NDIAG_ENOCONV;
+    if (done != DONE_CONV) {
+      set_error("PCG breakdown");
+      return NDIAG_EBREAKDOWN;
     }
     if (!recheck) break;
     x_is_zero = false;
@@ -413,7 +573,20 @@ extern "C" ndiag_status krylov_solve(ndiag* h, int method, int precond, int mode
     }
     if (!dev_x) ND_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
   }
+  // the per-iteration record: squared norms become norms relative to ||b||
+  const int nrec = std::min(iters, h->hist_cap);
+  if (fp64 && h->hist_user && nrec > 0 && method != NDIAG_STATIONARY)
+    ND_CUDA(cudaMemcpyAsync(h->hist_user, h->hist_dev, sizeof(double) * 4 * (size_t)nrec, cudaMemcpyDeviceToHost,
+                            h->stream));
   ND_CUDA(cudaStreamSynchronize(h->stream));
+  if (fp64 && h->hist_user && nrec > 0 && method != NDIAG_STATIONARY) {
+    const double bn = bnorm > 0 ? bnorm : 1.0;
+    for (int k = 0; k < nrec; ++k) {
+      double* e = h->hist_user + 4 * (size_t)k;
+      e[0] = std::sqrt(e[0]) / bn;
+      if (method == NDIAG_BICGSTAB) e[1] = std::sqrt(e[1]) / bn;
+    }
+  }
   ndiag_status ds = check_device_status(h);
   if (ds == NDIAG_OK && P.kind == NDIAG_PREC_MG && method != NDIAG_STATIONARY) ds = mg_check(h);
   if (ds != NDIAG_OK) st = ds;
@@ -425,4 +598,18 @@ extern "C" ndiag_status krylov_solve(ndiag* h, int method, int precond, int mode
     info->status = st;
   }
   return st;
+}
+
+extern "C" ndiag_status ndiag_set_history(ndiag* h, double* out, int capacity) {
+  if (!h || capacity < 0) return NDIAG_EINVAL;
+  dev_free(h->hist_dev, sizeof(double) * 4 * (size_t)h->hist_cap, h->stream);
+  h->hist_dev = nullptr;
+  h->hist_cap = 0;
+  h->hist_user = nullptr;
+  if (!out || capacity == 0) return NDIAG_OK;
+  h->hist_dev = (double*)dev_alloc(sizeof(double) * 4 * (size_t)capacity, h->stream);
+  if (!h->hist_dev) return NDIAG_ENOMEM;
+  h->hist_cap = capacity;
+  h->hist_user = out;
+  return NDIAG_OK;
 }

@@ -27,7 +27,7 @@ PREC_NONE, PREC_SSOR, PREC_ILU0, PREC_MG = 0, 1, 2, 3
 # every symbol include/ndiag.h declares
 EXPORTED = ["ndiag_set_allocator", "ndiag_last_error", "ndiag_create", "ndiag_destroy", "ndiag_cells",
             "ndiag_precision", "sor_sweep", "ssor_apply", "mg_apply", "ndiag_mg_levels", "ndiag_selftest_wait", "ilu0_factor", "ilu0_apply", "ndiag_residual",
-            "krylov_solve", "ndiag_tune_omega", "ndiag_profile", "ndiag_read_counters", "ilu0_apply_noalloc",
+            "krylov_solve", "ndiag_set_history", "ndiag_tune_omega", "ndiag_profile", "ndiag_read_counters", "ilu0_apply_noalloc",
             "ndiag_batch_create", "ndiag_batch_autotune", "ndiag_batch_tiles", "ndiag_batch_solve",
             "ndiag_batch_cells", "ndiag_batch_launches", "ndiag_batch_destroy",
             "ndiag_server_create", "serve_submit", "serve_poll", "ndiag_server_wait", "ndiag_server_stats",
@@ -108,6 +108,7 @@ def load(path: str = LIB_PATH):
     L.ilu0_apply_noalloc.argtypes = [P, P, P]
     L.ndiag_residual.argtypes = [P, P, P, P, ctypes.POINTER(D)]
     L.krylov_solve.argtypes = [P, I, I, I, P, D, I, P, P, ctypes.POINTER(SolveInfo)]
+    L.ndiag_set_history.argtypes = [P, P, I]
     L.ndiag_tune_omega.argtypes = [P, P, D, I, I, P, ctypes.POINTER(I)]
     L.ndiag_profile.argtypes = [P, I]
     L.ndiag_read_counters.argtypes = [P, ctypes.POINTER(Counters)]
@@ -261,15 +262,28 @@ class NDiag:
                     sweep_bytes=c.sweep_bytes)
 
     def solve(self, method, precond, b, x, rtol=1e-8, maxit=10000, omega=1.0, mode=DECOMPOSED,
-              raise_on_noconv=True):
-        """b, x: fp64 torch CUDA tensors or numpy arrays (host). x is updated."""
+              raise_on_noconv=True, history=0):
+        """b, x: fp64 torch CUDA tensors or numpy arrays (host). x is updated.
+        history=K > 0 records the first K iterations (ndiag_set_history) into
+        info["history"], an array of shape (min(iters, K), 4)."""
         info = SolveInfo()
-        st = self.L.krylov_solve(self.h, method, precond, mode, _ptr(_omega(omega, self.dim)), float(rtol),
-                                 int(maxit), _ptr(b), _ptr(x), ctypes.byref(info))
+        hist = None
+        if history:
+            hist = np.zeros((int(history), 4))
+            _check(self.L, self.L.ndiag_set_history(self.h, hist.ctypes.data, int(history)))
+        try:
+            st = self.L.krylov_solve(self.h, method, precond, mode, _ptr(_omega(omega, self.dim)), float(rtol),
+                                     int(maxit), _ptr(b), _ptr(x), ctypes.byref(info))
+        finally:
+            if hist is not None:
+                self.L.ndiag_set_history(self.h, None, 0)
         if st != OK and (raise_on_noconv or st != ENOCONV):
             _check(self.L, st)
-        return dict(iters=info.iterations, outer=info.outer, relres=info.relres, seconds=info.seconds,
-                    status=STATUS_NAMES[st])
+        out = dict(iters=info.iterations, outer=info.outer, relres=info.relres, seconds=info.seconds,
+                   status=STATUS_NAMES[st])
+        if hist is not None:
+            out["history"] = hist[: min(info.iterations, int(history))].copy()
+        return out
 
 
     def tune_omega(self, b, rtol=1e-8, maxit=20000, budget=60, omega=1.0):

@@ -302,3 +302,31 @@ def test_full_size_solve_meets_tolerance_and_oracle_count(nd, big):
     env = json.load(open(os.path.join(GOLDEN, "varcoef2048_envelope.json")))
     lo, hi = min(env["min"], gold["iters"]) - 1, max(env["max"], gold["iters"]) + 1
     assert lo <= info["iters"] <= hi, (info, lo, hi)
+
+
+@pytest.mark.parametrize("shape,stencil,sub", [((96, 80), 5, (3, 2)), ((31, 17), 5, (1, 1)),
+                                               ((24, 20, 18), 7, (2, 2, 2)), ((40, 33), 9, (2, 3))])
+def test_residual_matches_the_oracle_matvec(nd, shape, stencil, sub):
+    """ndiag_residual: r = b - A x element by element against b minus the
+    oracle's matrix-vector product, and the returned norm against ||r||."""
+    dim = len(shape)
+    N = int(np.prod(shape))
+    if stencil == 9:
+        diags = W.convdiff9(shape[0], 4.0, 0.7) if shape[0] == shape[1] else W.embed5in9(
+            W.diffusion2d(W.smoothed_lognormal_alpha(shape[0], shape[1], 5)))
+    elif dim == 3:
+        diags = W.poisson3d(*shape)
+    else:
+        diags = W.diffusion2d(W.smoothed_lognormal_alpha(shape[0], shape[1], 5))
+    b, x = W.uniform_rhs(N, 61), W.uniform_rhs(N, 62)
+    h = nd.NDiag(dim, shape, stencil, diags, sub, "fp64")
+    r = _t(np.zeros(N))
+    nrm = h.residual(_t(b), _t(x), r)
+    want = b - oracle.Problem(dim, shape, stencil, diags, sub).matvec(x)
+    got = r.cpu().numpy()
+    # rounding of a sum of `stencil` products and b, in any order: a few ulp of
+    # |b| + |A| |x| per cell
+    scale = np.abs(b) + oracle.Problem(dim, shape, stencil, np.abs(diags), sub).matvec(np.abs(x))
+    assert np.all(np.abs(got - want) <= 16 * 2.0 ** -53 * scale)
+    assert abs(nrm - np.linalg.norm(want)) <= 1e-13 * np.linalg.norm(want)
+    h.close()
