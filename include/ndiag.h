@@ -401,9 +401,16 @@ ndiag_status ndiag_read_counters(ndiag* h, ndiag_counters* out);
  *                        iterations per refinement step); b, x DEVICE double,
  *                        concatenated; x holds the initial guess; infos[p]
  *                        (HOST, count entries) per problem. Every step of an
- *                        iteration is one launch over all problems; chunks of
- *                        iterations are replayed from a captured CUDA graph.
+ *                        iteration is one launch over all problems; the inner
+ *                        iterations of a refinement step are one launch of a
+ *                        CUDA graph whose conditional while node runs until
+ *                        no problem is active.
  *                        NDIAG_ENOCONV if some problem missed rtol.
+ *   ndiag_batch_ssor_apply one application of the batch's preconditioner, the
+ *                        decomposed SSOR of Sec. 5 (SPD form, factor omega,
+ *                        fp32) of every problem in one launch per pass:
+ *                        z = M^-1 r; r, z DEVICE float, concatenated; z must
+ *                        not alias r. Synchronises.
  */
 typedef struct ndiag_batch ndiag_batch;
 ndiag_status ndiag_batch_create(ndiag_batch** out, int count, const int64_t* nx, const int64_t* ny,
@@ -412,6 +419,7 @@ ndiag_status ndiag_batch_autotune(ndiag_batch* b, const double* rhs);
 ndiag_status ndiag_batch_tiles(const ndiag_batch* b, int* tile);
 ndiag_status ndiag_batch_solve(ndiag_batch* b, double rtol, int maxit, const double* rhs, double* x,
                                ndiag_solve_info* infos);
+ndiag_status ndiag_batch_ssor_apply(ndiag_batch* b, const float* r, float* z);
 int64_t ndiag_batch_cells(const ndiag_batch* b);
 int64_t ndiag_batch_launches(const ndiag_batch* b);
 void ndiag_batch_destroy(ndiag_batch* b);

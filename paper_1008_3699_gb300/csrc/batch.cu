@@ -8,9 +8,10 @@
 // cells of one problem), and dot products are summed per problem in block
 // order (deterministic, so a problem's arithmetic does not depend on the
 // others in the batch). Per-problem scalars and convergence masks stay on the
-// device; chunks of inner iterations are captured once into a CUDA graph and
-// replayed, with one small device-to-host read per chunk. A converged problem
-// keeps its slot (alpha = 0), so the graph is static.
+// device. The inner iterations of a refinement step are one launch of a CUDA
+// graph whose conditional while node repeats a captured body of 8 iterations
+// until no problem is active (the device sets the condition); a converged
+// problem keeps its slot (alpha = 0), so the body is static.
 //
 // The subdomain partition ("tile") of every problem is chosen by an
 // autotuner: for each candidate tile side it times batched SSOR applies and
@@ -185,6 +186,7 @@ __global__ void k_reduce(int np, const int* blk0, const double* part, double* ou
 struct Scal {
   double *rz, *rr, *r0r0, *pq, *alpha, *beta, *bb, *rr64, *tmp;
   int *act, *oact, *iters, *outer, *nact;
+  int *inner, *maxit;  // iterations of the current inner loop, and its limit
 };
 
 // inner start: rz = (r, z) (in tmp); the inner stop threshold on (r, r):
@@ -236,6 +238,19 @@ __global__ void k_count(int np, const int* a, int* n) {
   if (threadIdx.x == 0) *n = cnt;
 }
 // outer step: relres = sqrt(rr64 / bb); outer-active = relres > rtol
+// End of a body of the inner while-loop (k iterations): the loop goes on
+// while some problem's inner iteration is active and the limit is not reached.
+__global__ void k_inner_cond(int np, Scal s, int k, cudaGraphConditionalHandle cond) {
+  int mine = 0;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) mine |= s.act[p];
+  const int any = __syncthreads_or(mine);
+  if (threadIdx.x == 0) {
+    const int n = *s.inner + k;
+    *s.inner = n;
+    cudaGraphSetConditional(cond, (any && n < *s.maxit) ? 1u : 0u);
+  }
+}
+
 __global__ void k_outer(int np, Scal s, double rtol) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
@@ -282,8 +297,7 @@ struct ndiag_batch {
   int* nact_host = nullptr;
   double omega = 1.0;
   BatchSweep fwd, rev, edges;
-  cudaGraphExec_t chunk = nullptr;
-  int chunk_k = 0;
+  cudaGraphExec_t loop = nullptr;  // the inner PCG loop: one conditional while node
   std::vector<void*> allocs;
   std::vector<size_t> alloc_bytes;
   int64_t launches = 0;
@@ -338,9 +352,9 @@ ndiag_status prepare_sweeps(ndiag_batch* B) {
   ND_TRY(batch_sweep_prepare(B->rev, hh.data(), np, KIND_TRI_UNIT, NDIAG_DECOMPOSED, tf ^ 1, om, 2, t.data(), nullptr,
                              z.data(), 1.0, true, B->stream));
   ND_TRY(batch_edges_prepare(B->edges, hh.data(), np, w, t.data(), z.data(), B->stream));
-  if (B->chunk) {
-    cudaGraphExecDestroy(B->chunk);
-    B->chunk = nullptr;
+  if (B->loop) {
+    cudaGraphExecDestroy(B->loop);
+    B->loop = nullptr;
   }
   return NDIAG_OK;
 }
@@ -373,12 +387,63 @@ ndiag_status count_active(ndiag_batch* B, const int* flags, int* n) {
   return NDIAG_OK;
 }
 
+// The inner PCG iterations as one executable graph: a conditional while node
+// whose body holds K iterations (every step one launch over all problems) and
+// the condition kernel. The body is captured from the stream.
+constexpr int LOOP_K = 8;
+ndiag_status build_loop(ndiag_batch* B) {
+  cudaGraph_t g = nullptr;
+  ND_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle cond;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np{};
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_status(e, "conditional while node");
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(B->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_status(e, "cudaStreamBeginCaptureToGraph(inner loop)");
+  }
+  const int64_t l0 = B->launches;
+  ndiag_status st = NDIAG_OK;
+  for (int k = 0; k < LOOP_K && st == NDIAG_OK; ++k) st = pcg_iteration(B, 1.0);
+  if (st == NDIAG_OK) {
+    k_inner_cond<<<1, 256, 0, B->stream>>>(B->np, B->sc, LOOP_K, cond);
+    e = cudaGetLastError();
+  }
+  cudaGraph_t got = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(B->stream, &got);
+  B->launches = l0;  // captured, not run
+  if (st == NDIAG_OK && e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&B->loop, g, 0);
+  cudaGraphDestroy(g);
+  if (st != NDIAG_OK) return st;
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    B->loop = nullptr;
+    return cuda_status(e != cudaSuccess ? e : e2, "inner loop graph");
+  }
+  return NDIAG_OK;
+}
+
 // Batched solve of every problem: x (device, concatenated) in/out.
 ndiag_status batch_solve(ndiag_batch* B, const double* b, double* x, double rtol, int maxit,
                          std::vector<int>& iters, std::vector<int>& outer, std::vector<double>& relres) {
   const Blocks bl = blocks(B);
   const int g = B->nblk, np = B->np, pg = (np + 127) / 128;
-  const double tol2 = 1.0;  // the per-problem inner thresholds are set by k_inner_init
+  {
+    const int lim = std::max(maxit, 1);
+    ND_CUDA(cudaMemcpyAsync(B->sc.maxit, &lim, sizeof(int), cudaMemcpyHostToDevice, B->stream));
+  }
   // ||b||^2 per problem
   ND_CUDA(cudaMemcpyAsync(B->b64, b, sizeof(double) * B->Ntot, cudaMemcpyDeviceToDevice, B->stream));
   ND_CUDA(cudaMemcpyAsync(B->x64, x, sizeof(double) * B->Ntot, cudaMemcpyDeviceToDevice, B->stream));
@@ -413,29 +478,12 @@ ndiag_status batch_solve(ndiag_batch* B, const double* b, double* x, double rtol
     k_inner_init<<<pg, 128, 0, B->stream>>>(np, B->sc, rtol);
     k_pupd<<<g, VT, 0, B->stream>>>(bl, B->sc.beta, B->z32, B->p32, 1);
     ND_CUDA(cudaGetLastError());
-    // inner iterations in captured chunks
-    const int K = 8;
-    if (!B->chunk) {
-      cudaGraph_t graph;
-      ND_CUDA(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
-      ndiag_status st = NDIAG_OK;
-      for (int k = 0; k < K && st == NDIAG_OK; ++k) st = pcg_iteration(B, tol2);
-      cudaError_t e = cudaStreamEndCapture(B->stream, &graph);
-      if (st != NDIAG_OK) return st;
-      ND_CUDA(e);
-      ND_CUDA(cudaGraphInstantiate(&B->chunk, graph, 0));
-      cudaGraphDestroy(graph);
-      B->chunk_k = K;
-    }
-    int done_inner = 0;
-    for (;;) {
-      ND_CUDA(cudaGraphLaunch(B->chunk, B->stream));
-      ++B->launches;
-      done_inner += B->chunk_k;
-      int n = 0;
-      ND_TRY(count_active(B, B->sc.act, &n));
-      if (n == 0 || done_inner >= maxit) break;
-    }
+    // the inner iterations: one launch of the while-loop graph (the device
+    // decides when they stop)
+    if (!B->loop) ND_TRY(build_loop(B));
+    ND_CUDA(cudaMemsetAsync(B->sc.inner, 0, sizeof(int), B->stream));
+    ND_CUDA(cudaGraphLaunch(B->loop, B->stream));
+    ++B->launches;
     k_correct<<<g, VT, 0, B->stream>>>(bl, B->x64, B->e32, B->sc.oact);
     ND_CUDA(cudaGetLastError());
   }
@@ -449,10 +497,9 @@ ndiag_status batch_solve(ndiag_batch* B, const double* b, double* x, double rtol
   ND_CUDA(cudaMemcpyAsync(rr.data(), B->sc.rr64, sizeof(double) * np, cudaMemcpyDeviceToHost, B->stream));
   ND_CUDA(cudaMemcpyAsync(bb.data(), B->sc.bb, sizeof(double) * np, cudaMemcpyDeviceToHost, B->stream));
   ND_CUDA(cudaStreamSynchronize(B->stream));
-  for (int p = 0; p < np; ++p) {
-    relres[p] = bb[p] > 0 ? std::sqrt(rr[p] / bb[p]) : 0.0;
-    outer[p] += 1;
-  }
+  // outer[p] counts the checks after which problem p stayed active, i.e. its
+  // refinement steps (inner solves), as ndiag_solve_info.outer of krylov_solve
+  for (int p = 0; p < np; ++p) relres[p] = bb[p] > 0 ? std::sqrt(rr[p] / bb[p]) : 0.0;
   for (ndiag* h : B->hs) ND_TRY(check_device_status(h));
   return NDIAG_OK;
 }
@@ -581,7 +628,7 @@ ndiag_status ndiag_batch_create(ndiag_batch** out, int count, const int64_t* nx,
   B->r64 = (double*)balloc(B, sizeof(double) * Nt);
   float** f32s[6] = {&B->r32, &B->e32, &B->p32, &B->q32, &B->z32, &B->t32};
   for (float** f : f32s) *f = (float*)balloc(B, sizeof(float) * Nt);
-  B->scal_bytes = sizeof(double) * 9 * count + sizeof(int) * (5 * count + 1);
+  B->scal_bytes = sizeof(double) * 9 * count + sizeof(int) * (5 * count + 3);
   B->scal_mem = balloc(B, B->scal_bytes);
   cudaMallocHost(&B->nact_host, sizeof(int));
   bool ok = B->prob && B->blk_pid && B->blk_start && B->blk0 && B->part && B->b64 && B->x64 && B->r64 &&
@@ -608,6 +655,8 @@ ndiag_status ndiag_batch_create(ndiag_batch** out, int count, const int64_t* nx,
   s.iters = iv + 2 * count;
   s.outer = iv + 3 * count;
   s.nact = iv + 4 * count;
+  s.inner = iv + 4 * count + 1;
+  s.maxit = iv + 4 * count + 2;
   cudaMemcpyAsync(B->prob, pr.data(), sizeof(BProb) * count, cudaMemcpyHostToDevice, B->stream);
   cudaMemcpyAsync(B->blk_pid, bp.data(), sizeof(int) * B->nblk, cudaMemcpyHostToDevice, B->stream);
   cudaMemcpyAsync(B->blk_start, bs.data(), sizeof(int64_t) * B->nblk, cudaMemcpyHostToDevice, B->stream);
@@ -669,9 +718,22 @@ ndiag_status ndiag_batch_solve(ndiag_batch* B, double rtol, int maxit, const dou
 int64_t ndiag_batch_cells(const ndiag_batch* B) { return B ? B->Ntot : 0; }
 int64_t ndiag_batch_launches(const ndiag_batch* B) { return B ? B->launches : 0; }
 
+// One batched SSOR apply (the preconditioner of the batched PCG) on caller
+// vectors: z = M^-1 r for every problem, through the solver's own buffers.
+ndiag_status ndiag_batch_ssor_apply(ndiag_batch* B, const float* r, float* z) {
+  if (!B || !r || !z) return NDIAG_EINVAL;
+  const size_t bytes = sizeof(float) * (size_t)B->Ntot;
+  ND_CUDA(cudaMemcpyAsync(B->r32, r, bytes, cudaMemcpyDeviceToDevice, B->stream));
+  ND_TRY(ssor_batch(B));
+  ND_CUDA(cudaMemcpyAsync(z, B->z32, bytes, cudaMemcpyDeviceToDevice, B->stream));
+  ND_CUDA(cudaStreamSynchronize(B->stream));
+  for (ndiag* h : B->hs) ND_TRY(check_device_status(h));
+  return NDIAG_OK;
+}
+
 void ndiag_batch_destroy(ndiag_batch* B) {
   if (!B) return;
-  if (B->chunk) cudaGraphExecDestroy(B->chunk);
+  if (B->loop) cudaGraphExecDestroy(B->loop);
   batch_sweep_free(B->fwd, B->stream);
   batch_sweep_free(B->rev, B->stream);
   batch_sweep_free(B->edges, B->stream);

@@ -29,6 +29,7 @@ EXPORTED = ["ndiag_set_allocator", "ndiag_last_error", "ndiag_create", "ndiag_de
             "ndiag_precision", "sor_sweep", "ssor_apply", "mg_apply", "ndiag_mg_levels", "ndiag_selftest_wait", "ilu0_factor", "ilu0_apply", "ndiag_residual",
             "krylov_solve", "ndiag_set_history", "ndiag_tune_omega", "ndiag_profile", "ndiag_read_counters", "ilu0_apply_noalloc",
             "ndiag_batch_create", "ndiag_batch_autotune", "ndiag_batch_tiles", "ndiag_batch_solve",
+            "ndiag_batch_ssor_apply",
             "ndiag_batch_cells", "ndiag_batch_launches", "ndiag_batch_destroy",
             "ndiag_server_create", "serve_submit", "serve_poll", "ndiag_server_wait", "ndiag_server_stats",
             "ndiag_server_destroy", "eikonal_create", "eikonal_destroy", "eikonal_sweep", "eikonal_solve"]
@@ -116,6 +117,7 @@ def load(path: str = LIB_PATH):
     L.ndiag_batch_autotune.argtypes = [P, P]
     L.ndiag_batch_tiles.argtypes = [P, P]
     L.ndiag_batch_solve.argtypes = [P, D, I, P, P, P]
+    L.ndiag_batch_ssor_apply.argtypes = [P, P, P]
     L.ndiag_batch_cells.argtypes = [P]
     L.ndiag_batch_cells.restype = L64
     L.ndiag_batch_launches.argtypes = [P]
@@ -334,6 +336,11 @@ class Batch:
         t = np.zeros(self.count, dtype=np.int32)
         _check(self.L, self.L.ndiag_batch_tiles(self.h, _ptr(t)))
         return t
+
+    def ssor_apply(self, r, z):
+        """z = M^-1 r for every problem (the batch's decomposed SSOR, fp32);
+        r, z: concatenated float32 CUDA tensors."""
+        _check(self.L, self.L.ndiag_batch_ssor_apply(self.h, _ptr(r), _ptr(z)))
 
     def solve(self, b, x, rtol=1e-8, maxit=20000, raise_on_noconv=True):
         """b, x: concatenated fp64 CUDA tensors; x is updated. Returns per-problem infos."""
