@@ -19,6 +19,9 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 NATURAL, DECOMPOSED = 0, 1
+# ilu0_factor only: the decomposed ordering with the full ILU(0) of the stencil
+# pattern inside every subdomain (modified off-diagonals; 9-point molecules)
+DECOMPOSED_FULL = 3
 PREC_NONE, PREC_SSOR, PREC_ILU0 = 0, 1, 2
 PCG, BICGSTAB, STATIONARY = 0, 1, 2
 

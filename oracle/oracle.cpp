@@ -26,6 +26,10 @@
 //                                      exactly (Eqs. 1d:sorc, 2d:sor4b4,
 //                                      2d:sor2b2; Sec. 4: 8x8/4x4/2x2 in 3D)
 //   ILU(0) ............................ Sec. 5 (SGS pass == ILU(0), Saad 10.3)
+//   decomposed full ILU(0) ............ Sec. 5 read per subdomain block: the
+//                                      IKJ elimination (Saad Alg. 10.4) of
+//                                      A's block in its sweep order, couplings
+//                                      across interfaces those of the sweep
 //   SSOR apply (SPD form) ............. Sec. 2 (SSOR = LR then RL), Sec. 5
 //   Krylov drivers .................... standard PCG / right-preconditioned
 //                                      BiCGSTAB (not from the paper)
@@ -36,7 +40,10 @@
 // Pins (tests/test_oracle_*.py): Table 1 iteration counts (1D GS natural and
 // decomposed), closed-form SOR/GS contraction rates on the Poisson model,
 // dense direct solves, the splitting equation, (LU)_ij = A_ij on the ILU(0)
-// pattern, SSOR symmetry and its dense closed form.
+// pattern, SSOR symmetry and its dense closed form; the full ILU(0): natural
+// IKJ with one subdomain, (LU)_ij = A_ij on every block's pattern, the
+// textbook ILU(1) of every block for 5-point matrices in 9-point storage, and
+// the apply against the dense product of its factors.
 // "parity unpinned": the decomposed sweep and ILU on the 9-point stencil
 // (the paper gives no detail beyond "straightforward", Sec. 3); only its
 // one-subdomain reduction and its convergence are checked.
@@ -178,7 +185,7 @@ int subdomain_corner(int d, int64_t t, const int idx[3]) {
 // ---------------------------------------------------------------------------
 // Problem handle.
 // ---------------------------------------------------------------------------
-enum { MODE_NATURAL = 0, MODE_DECOMPOSED = 1 };
+enum { MODE_NATURAL = 0, MODE_DECOMPOSED = 1, MODE_DECOMPOSED_FULL = 3 };
 
 struct Plan {
   bool built = false;
@@ -197,6 +204,7 @@ struct Problem {
   int ilu_mode = -1;
   std::vector<double> dtilde;    // decomposed ILU(0) pivots
   std::vector<double> lu;        // natural ILU(0): s x N, L multipliers / U
+  std::vector<double> full;      // decomposed full ILU(0): s x N in the form (D + L') D^-1 (D + U')
   // per-iteration record of the last Krylov solve, 4 values per iteration:
   // BiCGSTAB ||s||/||b||, ||r||/||b||, alpha, omega; PCG ||r||/||b||, alpha, 0, 0
   std::vector<double> hist;
@@ -373,7 +381,9 @@ bool dense_solve(int m, std::vector<double>& M, std::vector<double>& r, std::vec
 // transpose=true solves (Delta + L^T) x = g instead (the backward half of the
 // symmetric SSOR apply): blocks in reverse order, L^T(i,j) = L(j,i).
 bool block_solve(const Problem& pb, const Plan& pl, const double* Delta, const double* scale,
-                 const double* gvec, double* x, bool transpose) {
+                 const double* gvec, double* x, bool transpose, const double* E = nullptr) {
+  // E: the entries to use instead of A's (s x N, diagonal-major), or null
+  auto ent = [&](int k, int64_t i) { return E ? E[(size_t)k * pb.g.N + i] : aval(pb, k, i); };
   const Grid& g = pb.g;
   const int64_t nb = (int64_t)pl.bstart.size() - 1;
   std::vector<double> M, r, sol;
@@ -398,11 +408,11 @@ bool block_solve(const Problem& pb, const Plan& pl, const double* Delta, const d
         double coef;
         if (!transpose) {
           if (!(pl.jmask[i] >> k & 1)) continue;
-          coef = (scale ? scale[i] : 1.0) * aval(pb, k, i);
+          coef = (scale ? scale[i] : 1.0) * ent(k, i);
         } else {
           const int kb = g.opp[k];  // entry of row j that points back to i
           if (!(pl.jmask[j] >> kb & 1)) continue;
-          coef = (scale ? scale[j] : 1.0) * aval(pb, kb, j);
+          coef = (scale ? scale[j] : 1.0) * ent(kb, j);
         }
         const int c = pos(j);
         if (c >= 0) M[p * m + c] += coef;
@@ -475,10 +485,13 @@ int64_t fwd_phase(int d) { return d == 1 ? 0 : 1; }
 //  decomposed: M = (D~ + L_J) D~^-1 (D~ + U_J), L_J = implicit entries of the
 //              forward phase, U_J = implicit entries of its reverse phase, and
 //              d~_i = a_ii - sum_{j in J_i, i not in J_j} a_ij a_ji / d~_j.
+bool ilu0_factor_full(Problem& pb);
+
 bool ilu0_factor(Problem& pb, int mode) {
   const Grid& g = pb.g;
   const int64_t N = g.N;
   pb.ilu_mode = mode;
+  if (mode == MODE_DECOMPOSED_FULL) return ilu0_factor_full(pb);
   if (mode == MODE_DECOMPOSED) {
     Plan& pl = get_plan(pb, MODE_DECOMPOSED, fwd_phase(g.d));
     pb.dtilde.assign(N, 0.0);
@@ -552,9 +565,110 @@ bool ilu0_factor(Problem& pb, int mode) {
   return true;
 }
 
+// Decomposed full ILU(0) on the stencil's pattern (the 9-point molecule keeps
+// the elimination's updates of off-diagonal entries; Sec. 5 read as the ILU(0)
+// of every subdomain's diagonal block in the order its sweep visits it):
+// within every subdomain, the IKJ elimination (Saad Alg. 10.4) of A's
+// diagonal block in that subdomain's own order at the forward phase (its
+// reflected lexicographic order, the order of its sweep); entries that point
+// into another subdomain stay A's, and the apply couples across interfaces
+// exactly as the decomposed sweep does (mutual face pairs, Sec. 3). The factor
+// is kept as F (s x N) in the form M = (D + L') D^-1 (D + U'): F(0, i) = u_ii,
+// lower entries l_ij u_jj, upper entries u_ij. With one subdomain this is the
+// natural IKJ ILU(0); on 5/7-point matrices nothing but the pivots changes.
+bool ilu0_factor_full(Problem& pb) {
+  const Grid& g = pb.g;
+  const int64_t N = g.N;
+  const Plan& pl = get_plan(pb, MODE_DECOMPOSED, fwd_phase(g.d));
+  pb.full = pb.A;
+  auto F = [&](int k, int64_t i) -> double& { return pb.full[(size_t)k * N + i]; };
+  // the cells of every subdomain, each in its own sweep order
+  std::vector<int64_t> cells(N);
+  for (int64_t i = 0; i < N; ++i) cells[i] = i;
+  auto sub_of = [&](int64_t i) {
+    int64_t c[3];
+    coords(g, i, c);
+    return pb.P.part_of[0][c[0]] + (int64_t)pb.P.p[0] *
+           (pb.P.part_of[1][c[1]] + (int64_t)pb.P.p[1] * pb.P.part_of[2][c[2]]);
+  };
+  std::stable_sort(cells.begin(), cells.end(), [&](int64_t a, int64_t b) {
+    const int64_t sa = sub_of(a), sb = sub_of(b);
+    if (sa != sb) return sa < sb;
+    int64_t ca[3], cb[3];
+    coords(g, a, ca);
+    coords(g, b, cb);
+    return precedes(ca, cb, pl.corner[a]);
+  });
+  for (int64_t i : cells) {
+    int64_t ci[3];
+    coords(g, i, ci);
+    const int cs = pl.corner[i];
+    // entries of row i inside its subdomain, in the subdomain's order
+    int ks[27];
+    int64_t cols[27];
+    int m = 0;
+    for (int k = 0; k < g.s; ++k) {
+      const int64_t j = (k == 0) ? i : neighbour(g, i, k);
+      if (j < 0) continue;
+      int64_t cj[3];
+      coords(g, j, cj);
+      if (!same_part(pb, ci, cj)) continue;
+      ks[m] = k;
+      cols[m] = j;
+      ++m;
+    }
+    auto before = [&](int64_t a, int64_t b) {
+      int64_t ca[3], cb[3];
+      coords(g, a, ca);
+      coords(g, b, cb);
+      return precedes(ca, cb, cs);
+    };
+    for (int a = 0; a < m; ++a)
+      for (int b2 = a + 1; b2 < m; ++b2)
+        if (before(cols[b2], cols[a])) {
+          std::swap(cols[a], cols[b2]);
+          std::swap(ks[a], ks[b2]);
+        }
+    int nlow = 0;
+    for (int a = 0; a < m && cols[a] != i; ++a) {
+      const int64_t kc = cols[a];
+      ++nlow;
+      // a_ik := a_ik / a_kk
+      F(ks[a], i) /= F(0, kc);
+      const double lik = F(ks[a], i);
+      // every later entry j of row i that row k holds: a_ij -= a_ik a_kj
+      for (int b2 = a + 1; b2 < m; ++b2) {
+        const int64_t j = cols[b2];
+        for (int kk = 0; kk < g.s; ++kk) {
+          const int64_t jj = (kk == 0) ? kc : neighbour(g, kc, kk);
+          if (jj == j) {
+            F(ks[b2], i) -= lik * F(kk, kc);
+            break;
+          }
+        }
+      }
+    }
+    if (F(0, i) == 0.0) return false;
+    for (int a = 0; a < nlow; ++a) F(ks[a], i) *= F(0, cols[a]);  // l_ij u_jj
+  }
+  get_plan(pb, MODE_DECOMPOSED, fwd_phase(g.d) ^ 1);
+  return true;
+}
+
 bool ilu0_apply(Problem& pb, const double* r, double* z) {
   const Grid& g = pb.g;
   const int64_t N = g.N;
+  if (pb.ilu_mode == MODE_DECOMPOSED_FULL) {
+    const int64_t tf = fwd_phase(g.d);
+    Plan& pf = get_plan(pb, MODE_DECOMPOSED, tf);
+    Plan& pbk = get_plan(pb, MODE_DECOMPOSED, tf ^ 1);
+    const double* E = pb.full.data();
+    std::vector<double> d(E, E + N), y(N), dy(N);
+    // (D + L') y = r ; (D + U') z = D y, each with the decomposed sweep's couplings
+    if (!block_solve(pb, pf, d.data(), nullptr, r, y.data(), false, E)) return false;
+    for (int64_t i = 0; i < N; ++i) dy[i] = d[i] * y[i];
+    return block_solve(pb, pbk, d.data(), nullptr, dy.data(), z, false, E);
+  }
   if (pb.ilu_mode == MODE_DECOMPOSED) {
     const int64_t tf = fwd_phase(g.d);
     Plan& pf = get_plan(pb, MODE_DECOMPOSED, tf);
@@ -883,6 +997,9 @@ int orc_ilu0_factor(void* h, int mode) {
 
 // Decomposed: out[0..N) = d~. Natural: out[0..s*N) = L multipliers (entries
 // pointing to lower indices) and U (diagonal and upper entries), diagonal-major.
+// Decomposed full: out[0..s*N) = F, diagonal u_ii, lower entries l_ij u_jj,
+// upper entries u_ij (lower/upper in the subdomain's sweep order; entries
+// into another subdomain are A's).
 int orc_ilu0_export(void* h, double* out) {
   Problem& pb = *static_cast<Problem*>(h);
   if (pb.ilu_mode == MODE_DECOMPOSED) {
@@ -891,6 +1008,10 @@ int orc_ilu0_export(void* h, double* out) {
   }
   if (pb.ilu_mode == MODE_NATURAL) {
     std::memcpy(out, pb.lu.data(), sizeof(double) * pb.lu.size());
+    return 0;
+  }
+  if (pb.ilu_mode == MODE_DECOMPOSED_FULL) {
+    std::memcpy(out, pb.full.data(), sizeof(double) * pb.full.size());
     return 0;
   }
   return 1;
@@ -955,7 +1076,10 @@ int orc_solve(void* h, int method, int prec, int mode, const double* omega, doub
               int maxit, const double* b, double* x, double* info) {
   Problem& pb = *static_cast<Problem*>(h);
   pb.hist.clear();
-  if (prec == PREC_ILU0 && pb.ilu_mode != mode)
+  // an ILU(0) solve keeps the factor it finds in the same ordering (the full
+  // decomposed factor too); otherwise it factors first
+  const bool have = pb.ilu_mode == mode || (mode == MODE_DECOMPOSED && pb.ilu_mode == MODE_DECOMPOSED_FULL);
+  if (prec == PREC_ILU0 && !have)
     if (!ilu0_factor(pb, mode)) return 4;
   switch (method) {
     case METHOD_PCG: return pcg(pb, prec, mode, omega[0], rtol, maxit, b, x, info);

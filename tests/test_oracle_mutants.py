@@ -148,6 +148,40 @@ def pin_table5_ssour(L):
     return k == 58
 
 
+def pin_full_blocks(L):
+    """Decomposed full ILU(0): L U = A on every subdomain block's pattern."""
+    from tests.test_oracle_ilu_full import _block_lu, _blocks, _rand9
+    n, sub = (11, 9), (3, 2)
+    d = _rand9(n, 5)
+    pb = oracle.Problem(2, n, 9, d, sub, library=L)
+    pb.ilu0_factor(oracle.DECOMPOSED_FULL)
+    F = pb.ilu0_export()
+    nb = neighbours(full_n(n), 9)
+    A = assemble(full_n(n), 9, d).toarray()
+    for cells in _blocks(pb, n, sub).values():
+        Lb, Ub = _block_lu(F, nb, cells)
+        Ab = A[np.ix_(cells, cells)]
+        if np.max(np.abs((Lb @ Ub - Ab)[Ab != 0])) > 1e-12 * np.max(np.abs(Ab)):
+            return False
+    return True
+
+
+def pin_full_apply(L):
+    """Decomposed full ILU(0) apply inverts (D + L') D^-1 (D + U')."""
+    from tests.test_oracle_ilu_full import _rand9
+    n, sub = (10, 9), (2, 3)
+    pb = oracle.Problem(2, n, 9, _rand9(n, 8), sub, library=L)
+    pb.ilu0_factor(oracle.DECOMPOSED_FULL)
+    F = pb.ilu0_export()
+    tf = pb.fwd_phase()
+    fn = full_n(n)
+    Lp = assemble(fn, 9, F, jmask_bool(pb.plan_info(1, tf)[0], 9), include_diag=False).toarray()
+    Up = assemble(fn, 9, F, jmask_bool(pb.plan_info(1, tf ^ 1)[0], 9), include_diag=False).toarray()
+    M = (np.diag(F[0]) + Lp) @ np.diag(1.0 / F[0]) @ (np.diag(F[0]) + Up)
+    r = W.uniform_rhs(90, 3)
+    return np.max(np.abs(M @ pb.ilu0_apply(r) - r)) <= 1e-12 * np.max(np.abs(r))
+
+
 MUTANTS = [
     ("no interface coupling",
      "  return q_up_in_i && i_up_in_q;", "  return false;",
@@ -165,8 +199,8 @@ MUTANTS = [
      "    double acc = (1.0 - wi) * aii * u[i] + wi * b[i];", "    double acc = wi * b[i];",
      [pin_splitting]),
     ("transposed solve uses the row's own entry",
-     "          coef = (scale ? scale[j] : 1.0) * aval(pb, kb, j);",
-     "          coef = (scale ? scale[i] : 1.0) * aval(pb, k, i);",
+     "          coef = (scale ? scale[j] : 1.0) * ent(kb, j);",
+     "          coef = (scale ? scale[i] : 1.0) * ent(k, i);",
      [pin_ssor_symmetric]),
     ("decomposed ILU uses a_ij twice",
      "          acc -= aval(pb, k, i) * aval(pb, kb, j) / pb.dtilde[j];",
@@ -175,6 +209,19 @@ MUTANTS = [
     ("natural ILU divides by the wrong pivot",
      "      L(ks[a], i) /= L(0, kc);", "      L(ks[a], i) /= L(0, i);",
      [lambda L: pin_ilu_pattern(L, 0)]),
+    ("full ILU drops the update of later entries",
+     "            F(ks[b2], i) -= lik * F(kk, kc);", "            (void)lik;",
+     [pin_full_blocks]),
+    ("full ILU stores l_ij instead of l_ij u_jj",
+     "    for (int a = 0; a < nlow; ++a) F(ks[a], i) *= F(0, cols[a]);  // l_ij u_jj", "",
+     [pin_full_blocks]),
+    ("full ILU eliminates in the natural order in every subdomain",
+     "      return precedes(ca, cb, cs);", "      return precedes(ca, cb, 0);",
+     [pin_full_blocks]),
+    ("full ILU apply solves the forward phase twice",
+     "    return block_solve(pb, pbk, d.data(), nullptr, dy.data(), z, false, E);",
+     "    return block_solve(pb, pf, d.data(), nullptr, dy.data(), z, false, E);",
+     [pin_full_apply]),
     ("BiCGSTAB drops the omega step from x",
      "      for (int64_t i = 0; i < N; ++i) x[i] += alpha * ph[i] + om * sh[i];",
      "      for (int64_t i = 0; i < N; ++i) x[i] += alpha * ph[i];",
