@@ -62,7 +62,10 @@ enum {
 /* Ordering of a sweep. */
 enum {
   NDIAG_NATURAL = 0,    /* lexicographic order over the whole grid */
-  NDIAG_DECOMPOSED = 1  /* the paper's decomposed multi-frontal order */
+  NDIAG_DECOMPOSED = 1, /* the paper's decomposed multi-frontal order */
+  /* ilu0_factor only: the decomposed order with the full ILU(0) of every
+   * subdomain's block (modified off-diagonals on the 9-point molecule) */
+  NDIAG_DECOMPOSED_FULL = 3
 };
 
 enum { NDIAG_PCG = 0, NDIAG_BICGSTAB = 1, NDIAG_STATIONARY = 2 };
@@ -233,6 +236,16 @@ ndiag_status eikonal_solve(ndiag_eik* e, double* u, double delta, int max_rounds
  * matrix stored as a 9-point one with zero corner entries gets its ILU(1)
  * this way: in natural order its level-1 fill is exactly the (x+1, y-1) and
  * (x-1, y+1) positions, and the other corners never fill.
+ * DECOMPOSED_FULL: inside every subdomain the true ILU(0) of A's diagonal
+ * block in the order that subdomain's forward sweep visits it (its
+ * lexicographic order reflected along the axes it sweeps backwards), IKJ on
+ * the stencil pattern as above; entries into another subdomain keep A's
+ * values, and the apply couples across interfaces as the decomposed sweep
+ * does (mutual face pairs solved together). Applied as (D + L') D^-1 (D + U')
+ * with the decomposed sweeps of the forward phase and its reverse. With one
+ * subdomain it is the natural 9-point factor; a 5-point matrix in 9-point
+ * storage gets the decomposed ILU(1); on 5/7-point matrices it equals
+ * DECOMPOSED (only the pivots change).
  * Errors: NDIAG_EBREAKDOWN on a zero pivot (reported at the next sync).
  */
 ndiag_status ilu0_factor(ndiag* h, int mode);

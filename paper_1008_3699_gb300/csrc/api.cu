@@ -433,17 +433,23 @@ ndiag_status sor_sweep(ndiag* h, int mode, const double* omega, int64_t t, const
 }
 
 ndiag_status ilu0_factor(ndiag* h, int mode) {
-  if (!h || (mode != NDIAG_NATURAL && mode != NDIAG_DECOMPOSED)) return NDIAG_EINVAL;
-  if (h->stencil == 9 && mode == NDIAG_NATURAL) {
-    // true ILU(0) with modified off-diagonals, as a 9 x N matrix (D + L') D^-1 (D + U')
+  if (!h || (mode != NDIAG_NATURAL && mode != NDIAG_DECOMPOSED && mode != NDIAG_DECOMPOSED_FULL))
+    return NDIAG_EINVAL;
+  // on 5/7-point matrices the full factor of every subdomain block changes
+  // only the pivots, exactly as the decomposed one does
+  if (mode == NDIAG_DECOMPOSED_FULL && h->stencil != 9) mode = NDIAG_DECOMPOSED;
+  if (h->stencil == 9 && mode != NDIAG_DECOMPOSED) {
+    // true ILU(0) with modified off-diagonals, as a 9 x N matrix (D + L') D^-1 (D + U'):
+    // of the whole lexicographic order, or of every subdomain block in its sweep order
     const size_t fb = sizeof(double) * 9 * (size_t)h->N;
     double* F = (double*)dev_alloc(fb, h->stream);
     if (!F) return NDIAG_ENOMEM;
-    ndiag_status st = launch_ilu_factor9_natural(h, F);
+    ndiag_status st = mode == NDIAG_NATURAL ? launch_ilu_factor9_natural(h, F) : launch_ilu_factor9_full(h, F);
     if (st == NDIAG_OK) st = build_scaled_from(h, h->ilu, F, F);
     dev_free(F, fb, h->stream);
     if (st == NDIAG_OK) st = check_status(h);
-    h->ilu_mode = st == NDIAG_OK ? mode : -1;
+    // the full factor is applied by the decomposed sweeps
+    h->ilu_mode = st == NDIAG_OK ? (mode == NDIAG_NATURAL ? NDIAG_NATURAL : NDIAG_DECOMPOSED) : -1;
     return st;
   }
   double* dt = (double*)dev_alloc(sizeof(double) * (size_t)h->N, h->stream);

@@ -188,6 +188,9 @@ ndiag_status build_scaled(Handle* h, ScaledSet& set, const double* piv);
 ndiag_status build_scaled_from(Handle* h, ScaledSet& set, const double* A, const double* piv);
 // natural-order ILU(0) of a 9-point matrix into F (9 x N, ilu9n.cu)
 ndiag_status launch_ilu_factor9_natural(Handle* h, double* F);
+// decomposed full ILU(0) of a 9-point matrix into F (9 x N, ilu9n.cu): the
+// IKJ elimination of every subdomain's block in its forward-sweep order
+ndiag_status launch_ilu_factor9_full(Handle* h, double* F);
 // One prepared launch of the staged 2D sweep over several handles (a batch of
 // independent problems): device arrays of per-problem parameters and slab
 // offsets, rebuilt by batch_sweep_prepare, launched by batch_sweep_launch

@@ -21,6 +21,8 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ENOCONV", "EBREAKDOWN", "EDEVICE", "E
 FP64, FP32, FP32_D16 = 0, 1, 2
 PRECISION = {"fp64": FP64, "fp32": FP32, "fp32_d16": FP32_D16}
 NATURAL, DECOMPOSED = 0, 1
+# ilu0_factor only: full ILU(0) of every subdomain block (9-point: modified off-diagonals)
+DECOMPOSED_FULL = 3
 PCG, BICGSTAB, STATIONARY = 0, 1, 2
 PREC_NONE, PREC_SSOR, PREC_ILU0, PREC_MG = 0, 1, 2, 3
 
