@@ -674,7 +674,7 @@ def workload_serving(args):
     # the 9-point sweep alone: ILU(0) applies of the largest request size
     n9 = 2048
     h9 = nd.NDiag(2, (n9, n9), 9, W.convdiff9(n9, 6.0, 1.1), (16, 16), "fp64")
-    h9.ilu0_factor(nd.DECOMPOSED)
+    h9.ilu0_factor(nd.DECOMPOSED_FULL)  # the served factor
     r9 = torch.tensor(W.uniform_rhs(n9 * n9, 5), device="cuda")
     z9 = torch.empty_like(r9)
     for _ in range(2):

@@ -449,7 +449,9 @@ void ndiag_batch_destroy(ndiag_batch* b);
  *                        fits the remaining budget (first fitting request in
  *                        arrival order; one larger than the whole budget runs
  *                        alone). Always decomposed ordering with sub[];
- *                        ILU0 requests are factored first.
+ *                        ILU0 requests are factored first, with
+ *                        DECOMPOSED_FULL (on 9-point matrices the full ILU(0)
+ *                        of every subdomain block; 5/7-point: DECOMPOSED).
  *   serve_poll           NDIAG_EBUSY while the request is queued or running;
  *                        then fills *out, copies x (HOST, N doubles) if x is
  *                        not NULL, and forgets the ticket.

@@ -75,7 +75,9 @@ void run_job(Job& j, cudaStream_t s) {
     dev = (double*)nd::dev_alloc(sizeof(double) * 2 * (size_t)N, s);
     if (!dev) st = NDIAG_ENOMEM;
   }
-  if (st == NDIAG_OK && r.precond == NDIAG_PREC_ILU0) st = ilu0_factor(h, NDIAG_DECOMPOSED);
+  // the full factor of every subdomain block: on 9-point matrices it needs about a
+  // third fewer BiCGSTAB iterations than D-ILU; on 5/7-point ones it is the same factor
+  if (st == NDIAG_OK && r.precond == NDIAG_PREC_ILU0) st = ilu0_factor(h, NDIAG_DECOMPOSED_FULL);
   if (st == NDIAG_OK) {
     cudaMemcpyAsync(dev, j.b.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(dev + N, 0, sizeof(double) * N, s);
