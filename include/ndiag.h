@@ -396,6 +396,16 @@ ndiag_status ndiag_profile(ndiag* h, int enable);
 ndiag_status ndiag_read_counters(ndiag* h, ndiag_counters* out);
 
 /*
+ * ndiag_set_sweep9_kernel -- which kernel runs the fp64 decomposed 9-point
+ * triangular sweeps (the ILU(0) apply): wave != 0 (default) the warp-
+ * synchronous wavefront (lane = row, packed coefficient copy built on first
+ * use per coefficient set and phase), wave == 0 the level-by-level kernel.
+ * Both compute the same sweep (Sec. 3); their roundings differ. Subdomains
+ * taller than 129 rows always take the level kernel.
+ */
+ndiag_status ndiag_set_sweep9_kernel(ndiag* h, int wave);
+
+/*
  * Batched solves of many independent 2D 5-point problems (the paper has no
  * counterpart: a GPU serving pattern around its decomposed SSOR). Each problem
  * is a diagonal-major matrix (5 x nx[p]*ny[p], HOST, caller keeps ownership);

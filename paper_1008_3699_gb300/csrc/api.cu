@@ -370,6 +370,7 @@ void ndiag_destroy(ndiag* h) {
   if (!h) return;
   cudaStream_t s = h->stream;
   mg_free(h);
+  w9pack_free(h);
   dev_free(h->A64, 0, s);
   dev_free(h->Alo, 0, s);
   dev_free(h->sor.base, h->sor.bytes, s);
@@ -408,6 +409,12 @@ ndiag_status ndiag_profile(ndiag* h, int enable) {
   h->sweep_ms = 0.0;
   h->sweep_bytes = 0.0;
   h->profiling = enable != 0;
+  return NDIAG_OK;
+}
+
+ndiag_status ndiag_set_sweep9_kernel(ndiag* h, int wave) {
+  if (!h) return NDIAG_EINVAL;
+  h->w9_wave = wave != 0;
   return NDIAG_OK;
 }
 

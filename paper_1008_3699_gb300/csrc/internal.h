@@ -92,6 +92,20 @@ struct ProfRec {
 
 struct Multigrid;  // mg.cu
 
+// Packed copy of a scaled set for the 9-point wavefront sweeps (sweep9w.cu):
+// one per phase and kind, rebuilt when the set or the partition changes.
+struct W9Pack {
+  const void* set_base = nullptr;
+  unsigned set_version = 0;
+  int64_t t = -1;
+  int kind = -1;
+  int sub0 = 0, sub1 = 0;
+  double* buf = nullptr;
+  size_t bytes = 0;
+  double* rdx = nullptr;
+  size_t rdx_bytes = 0;
+};
+
 struct Handle {
   int dim = 0, stencil = 0, precision = 0;
   int64_t n[3] = {1, 1, 1};
@@ -139,6 +153,8 @@ struct Handle {
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> ev_pool;
   Multigrid* mg = nullptr;       // V-cycle hierarchy (built on the first multigrid apply)
+  std::vector<W9Pack> w9pack;    // 9-point wavefront operands (sweep9w.cu)
+  bool w9_wave = true;           // use the wavefront kernel where it applies
 };
 
 // Sweep-launch timing: brackets a sweep kernel with events when profiling is
@@ -231,6 +247,11 @@ ndiag_status launch_ilu_factor3d_into(Handle* h, int mode, double* out);
 ndiag_status launch_sweep9(Handle* h, int kind, int mode, int64_t t, const double* omega, const ScaledSet& set,
                            const void* rhs, const void* xold, void* xnew, double beta_scale);
 ndiag_status launch_ilu_factor9_into(Handle* h, int mode, double* out);
+// fp64 decomposed 9-point triangular sweeps as a warp-synchronous wavefront
+// (sweep9w.cu); NDIAG_EINVAL, with nothing launched, outside its cover
+ndiag_status launch_sweep9w(Handle* h, int kind, int mode, int64_t t, const ScaledSet& set, const void* rhs,
+                            void* xnew);
+void w9pack_free(Handle* h);
 ndiag_status build_scaled_transposed(Handle* h, ScaledSet& set);
 
 // BLAS-1 and SpMV (blas.cu)

@@ -494,6 +494,12 @@ ndiag_status sweep9_t(Handle* h, int kind, int mode, int64_t t, const double* om
 
 ndiag_status launch_sweep9(Handle* h, int kind, int mode, int64_t t, const double* omega, const ScaledSet& set,
                            const void* rhs, const void* xold, void* xnew, double beta_scale) {
+  // fp64 decomposed triangular sweeps without relaxation: the wavefront kernel
+  if (kind != KIND_SOR && !omega && beta_scale == 1.0 && h->precision == NDIAG_FP64 && mode == NDIAG_DECOMPOSED &&
+      h->w9_wave) {
+    const ndiag_status st = launch_sweep9w(h, kind, mode, t, set, rhs, xnew);
+    if (st != NDIAG_EINVAL) return st;
+  }
   switch (h->precision) {
     case NDIAG_FP64: return sweep9_t<double, double>(h, kind, mode, t, omega, set, rhs, xold, xnew, beta_scale);
     case NDIAG_FP32: return sweep9_t<float, float>(h, kind, mode, t, omega, set, rhs, xold, xnew, beta_scale);
