@@ -185,7 +185,7 @@ def main():
                     help="only factor and run K ILU(0) applies of the workload (for kernel profiling)")
     ap.add_argument("--workload", default="varcoef2048",
                     choices=["varcoef2048", "poisson64", "poisson3d", "batch512", "serving", "mg2048",
-                             "eikonal2048", "mg3d"],
+                             "eikonal2048", "mg3d", "convdiff9"],
                     help="varcoef2048 is the benchmark; the others print one measurement line each")
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--n3d", type=int, default=256, help="side of the 3D Poisson workload (subdomains of 32^3)")
@@ -886,9 +886,61 @@ def workload_mg3d(args):
                       "ssor_pcg": {k: ssor[k] for k in ("iters", "relres", "wall_s")}, "cpu_baseline": cpu}))
 
 
+
+def workload_convdiff9(args):
+    """The largest served 9-point request: 2048^2 nonsymmetric convection-
+    diffusion (Peclet 6, angle 1.1), 16 x 16 subdomains, fp64 BiCGSTAB with the
+    decomposed full ILU(0) (and with D-ILU) to rel-res 1e-8; the ILU(0) apply
+    timed with CUDA events for the wavefront and the level kernels.
+    --kernel-only K: factor, then K applies (for kernel profiling)."""
+    torch, nd, W = _setup()
+    n = 2048
+    d = W.convdiff9(n, 6.0, 1.1)
+    b = torch.tensor(W.uniform_rhs(n * n, 5), device="cuda")
+    peak, kind = measured_peaks()
+    if args.kernel_only:
+        h = nd.NDiag(2, (n, n), 9, d, (16, 16), "fp64")
+        h.ilu0_factor(nd.DECOMPOSED_FULL)
+        z = torch.empty_like(b)
+        for _ in range(args.kernel_only):
+            h.ilu0_apply(b, z)
+        torch.cuda.synchronize()
+        h.close()
+        print(json.dumps({"workload": "convdiff9-2048^2-kernel-only", "applies": args.kernel_only}))
+        return
+    # bytes of one apply per cell: forward inv, 4 entries, r, y; backward 4 entries, y, z
+    bpc = (5 * 8 + 2 * 8) + (4 * 8 + 2 * 8)
+    out = {"workload": "convdiff9-2048^2-pe6-16x16-fp64-bicgstab-ilu0", "metric": "solve seconds; apply GB/s"}
+    for name, mode, wave in (("full_ilu0", nd.DECOMPOSED_FULL, True), ("dilu", nd.DECOMPOSED, True),
+                             ("full_ilu0_level_kernel", nd.DECOMPOSED_FULL, False)):
+        h = nd.NDiag(2, (n, n), 9, d, (16, 16), "fp64")
+        h.set_wavefront(wave)
+        h.ilu0_factor(mode)
+        z = torch.empty_like(b)
+        for _ in range(3):
+            h.ilu0_apply(b, z)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(10):
+            h.ilu0_apply(b, z)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        gbs = bpc * n * n / (ms / 1e3) / 1e9
+        rec = {"apply_ms": ms, "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                            "frac": gbs / peak, "bytes_per_cell": bpc, "peak_kind": kind}}
+        if name != "full_ilu0_level_kernel" or not args.no_natural:
+            x = torch.zeros_like(b)
+            info = _timed_solve(torch, h, nd.BICGSTAB, nd.PREC_ILU0, b, x, rtol=1e-8, maxit=20000)
+            rec.update(iters=info["iters"], relres=info["relres"], seconds=info["wall_s"])
+        h.close()
+        out[name] = rec
+    print(json.dumps(out))
+
 EXTRA = {"poisson64": workload_poisson64, "poisson3d": workload_poisson3d,
          "batch512": workload_batch512, "serving": workload_serving, "mg2048": workload_mg2048,
-         "eikonal2048": workload_eikonal2048, "mg3d": workload_mg3d}
+         "eikonal2048": workload_eikonal2048, "mg3d": workload_mg3d, "convdiff9": workload_convdiff9}
 
 
 if __name__ == "__main__":

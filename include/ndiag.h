@@ -396,14 +396,15 @@ ndiag_status ndiag_profile(ndiag* h, int enable);
 ndiag_status ndiag_read_counters(ndiag* h, ndiag_counters* out);
 
 /*
- * ndiag_set_sweep9_kernel -- which kernel runs the fp64 decomposed 9-point
- * triangular sweeps (the ILU(0) apply): wave != 0 (default) the warp-
- * synchronous wavefront (lane = row, packed coefficient copy built on first
- * use per coefficient set and phase), wave == 0 the level-by-level kernel.
- * Both compute the same sweep (Sec. 3); their roundings differ. Subdomains
- * taller than 129 rows always take the level kernel.
+ * ndiag_set_wavefront -- on != 0 (default): the warp-synchronous wavefront
+ * kernels run (lane = row) where they apply: the fp64 decomposed 9-point
+ * triangular sweeps (the ILU(0) apply; packed coefficient copy built on first
+ * use per coefficient set and phase; subdomains up to 129 rows) and the
+ * one-cell part of the 3D 7-point triangular sweeps (a warp per plane;
+ * subdomains up to 32 x 32 in y and z). on == 0: the level-by-level kernels.
+ * Both compute the same sweep (Secs. 3, 4); their roundings differ.
  */
-ndiag_status ndiag_set_sweep9_kernel(ndiag* h, int wave);
+ndiag_status ndiag_set_wavefront(ndiag* h, int on);
 
 /*
  * Batched solves of many independent 2D 5-point problems (the paper has no

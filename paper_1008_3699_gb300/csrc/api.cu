@@ -412,9 +412,10 @@ ndiag_status ndiag_profile(ndiag* h, int enable) {
   return NDIAG_OK;
 }
 
-ndiag_status ndiag_set_sweep9_kernel(ndiag* h, int wave) {
+ndiag_status ndiag_set_wavefront(ndiag* h, int on) {
   if (!h) return NDIAG_EINVAL;
-  h->w9_wave = wave != 0;
+  h->w9_wave = on != 0;
+  h->w3_wave = on != 0;
   return NDIAG_OK;
 }
 

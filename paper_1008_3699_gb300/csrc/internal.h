@@ -154,7 +154,8 @@ struct Handle {
   std::vector<cudaEvent_t> ev_pool;
   Multigrid* mg = nullptr;       // V-cycle hierarchy (built on the first multigrid apply)
   std::vector<W9Pack> w9pack;    // 9-point wavefront operands (sweep9w.cu)
-  bool w9_wave = true;           // use the wavefront kernel where it applies
+  bool w9_wave = true;           // 9-point wavefront sweeps where they apply
+  bool w3_wave = true;           // 3D wavefront pencil walks where they apply
 };
 
 // Sweep-launch timing: brackets a sweep kernel with events when profiling is

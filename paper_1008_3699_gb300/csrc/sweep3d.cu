@@ -623,6 +623,153 @@ __global__ void __launch_bounds__(GT, 4) sweep3d_pencil_kernel(GP<T, TC> P) {
   }
 }
 
+// Wavefront form of the pencil walk (subdomains with h, d <= 32): warp z owns
+// the plane z and lane y its row y, and at step s lane y meets column
+// x = s - y. The x neighbour is the lane's previous cell (register), the y
+// neighbour arrives by shuffle from lane y - 1 (its previous step), the z
+// neighbour from warp z - 1 through a ring of a few steps in shared memory
+// (full / empty mbarriers per chunk, all 32 lanes arriving). A warp runs one
+// chunk behind the warp below it, so the walk takes about (w + h + d) chunks'
+// worth of steps instead of w + h + d block barriers. The transposed pass runs
+// the same walk in the reflected frame (dependents instead of predecessors).
+// Operands of the next chunk are loaded before the current one is computed;
+// the arithmetic of a cell is that of sweep3d_pencil_kernel.
+template <class T>
+struct WvCfg {
+  static constexpr int CH = 2;                        // steps per chunk (register double buffer)
+  static constexpr int R = sizeof(T) == 8 ? 8 : 16;   // ring slots (steps)
+  static constexpr int NS = R / CH;                   // ring stages
+};
+
+template <class T, class TC, int KIND, bool OM1>
+__global__ void __launch_bounds__(1024) sweep3d_wave_kernel(GP<T, TC> P) {
+  constexpr int CH = WvCfg<T>::CH, NS = WvCfg<T>::NS, WV_R = WvCfg<T>::R;
+  extern __shared__ __align__(16) unsigned char gsm[];
+  const Sub S = subdomain(P, blockIdx.x);
+  const int w = S.len[0], h = S.len[1], d = S.len[2];
+  const int nw = blockDim.x >> 5;
+  T* ring = reinterpret_cast<T*>(gsm);  // [nw][WV_R][32]
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(gsm + sizeof(T) * (size_t)nw * WV_R * 32);
+  unsigned long long* empty = full + nw * NS;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2 * nw * NS; ++i) mb_init(&full[i], 32);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int wz = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (wz >= d) return;
+  const bool tr = P.transposed != 0;
+  const bool row_on = lane < h;
+  const int y = tr ? h - 1 - lane : lane, z = tr ? d - 1 - wz : wz;
+  const int yc = row_on ? y : 0;
+  const int tcode = S.t[0] | (S.t[1] << 1) | (S.t[2] << 2);
+  const T om = OM1 ? T(1) : P.om[S.c[0] | (S.c[1] << 1) | (S.c[2] << 2)];
+  const int64_t rowbase = (int64_t)S.gco(1, yc) * P.stride[1] + (int64_t)S.gco(2, z) * P.stride[2];
+  const int yr = (P.lev_flip & 2) ? h - 1 - yc : yc, zr = (P.lev_flip & 4) ? d - 1 - z : z;
+  const int64_t ca = P.lev ? P.lev_arr : (int64_t)(P.c[0] - P.inv);
+  const int nsteps = w + h - 1, nch = (nsteps + CH - 1) / CH;
+  // Per-lane operand pointers at column xq = 0 of the walk and their step
+  // along it: the natural index moves by +-1, the level-ordered one by
+  // +-h0 d0 (one level) per column.
+  const int x0 = tr ? w - 1 : 0;
+  const int64_t gi0 = rowbase + S.gco(0, x0);
+  const int dgi = (S.gco(0, x0 + (tr ? -1 : 1)) - S.gco(0, x0));
+  const T* prhs = P.rhs + gi0;
+  const T* pxn = P.xnew + gi0;
+  int64_t ci0;
+  int dci;
+  if (P.lev) {
+    const int xr0 = (P.lev_flip & 1) ? w - 1 - x0 : x0;
+    ci0 = (int64_t)blockIdx.x * P.lev_sub + (int64_t)(xr0 + yr + zr) * P.lev_hd0 + yr + P.lev_h0 * zr;
+    const int xr1 = (P.lev_flip & 1) ? w - 1 - (x0 + (tr ? -1 : 1)) : x0 + (tr ? -1 : 1);
+    dci = (xr1 - xr0) * P.lev_hd0;
+  } else {
+    ci0 = gi0;
+    dci = dgi;
+  }
+  const TC* cb = (P.lev ? P.lev : P.inv) + ci0;
+  const TC* pinv = cb;
+  const TC* pg0 = cb + (1 + ent(0, (S.c[0] ^ tr) ? 1 : 0)) * ca;
+  const TC* pg1 = cb + (1 + ent(1, (S.c[1] ^ tr) ? 1 : 0)) * ca;
+  const TC* pg2 = cb + (1 + ent(2, (S.c[2] ^ tr) ? 1 : 0)) * ca;
+  // neighbours along y and z exist for the whole row; along x from column 1 on
+  const bool has_y = lane >= 1, has_z = wz > 0;
+  // coupled cells: the whole row (a coupled start face in y or z), or column 0 of the walk (in x)
+  const bool row_blk = (((y == 0) << 1 | (z == 0) << 2) & tcode) != 0;
+  const int xq_blk = (tcode & 1) ? (tr ? w - 1 : 0) : -1;  // walk column of the x-start face, if coupled
+  // operands of a chunk: inv, rhs (or the block's value), couplings x, y, z;
+  // cur is computed while nxt is loaded
+  struct Ops {
+    T i[CH], r[CH], g[3][CH];
+    unsigned blk;
+  };
+  auto fetch = [&](int k, Ops& o) {
+    o.blk = 0;
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      const int xq = k * CH + j - lane;  // column in the walk's frame
+      o.i[j] = T(0);
+      o.r[j] = T(0);
+      o.g[0][j] = o.g[1][j] = o.g[2][j] = T(0);
+      if (!row_on || xq < 0 || xq >= w) continue;
+      if (row_blk || xq == xq_blk) {  // a coupled block: the block launch's value (forward), or left to later passes
+        o.blk |= 1u << j;
+        if (!tr) o.r[j] = __ldcg(pxn + xq * dgi);
+        continue;
+      }
+      const int oc = xq * dci;
+      if (!tr && KIND == KIND_TRI_SCALED) o.i[j] = ldco<T, TC>(pinv + oc);
+      o.r[j] = __ldg(prhs + xq * dgi);
+      if (xq >= 1) o.g[0][j] = ldco<T, TC>(pg0 + oc);
+      if (has_y) o.g[1][j] = ldco<T, TC>(pg1 + oc);
+      if (has_z) o.g[2][j] = ldco<T, TC>(pg2 + oc);
+    }
+  };
+  T* ring_out = ring + (size_t)wz * WV_R * 32;
+  const T* ring_in = ring + (size_t)(wz > 0 ? wz - 1 : 0) * WV_R * 32;
+  const bool has_in = wz > 0, has_out = wz + 1 < d;
+  bool ok = true;
+  T xp = T(0);
+  Ops cur, nxt;
+  fetch(0, nxt);
+  for (int k = 0; k < nch; ++k) {
+    cur = nxt;
+    if (k + 1 < nch) fetch(k + 1, nxt);
+    const int st = k % NS;
+    if (has_in && ok) ok = mb_wait(&full[(wz - 1) * NS + st], (k / NS) & 1, P.st);
+    if (has_out && ok && k >= NS) ok = mb_wait(&empty[wz * NS + st], ((k / NS) - 1) & 1, P.st);
+    if (!ok) return;
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      const int s = k * CH + j, xq = s - lane;
+      const T sh = __shfl_up_sync(FULL, xp, 1);
+      const bool act = row_on && xq >= 0 && xq < w;
+      T v;
+      if ((cur.blk >> j) & 1) {
+        v = cur.r[j];
+      } else {
+        T acc = (!tr && KIND == KIND_TRI_SCALED) ? cur.i[j] * cur.r[j] : cur.r[j];
+        if (!OM1 && !tr && KIND == KIND_TRI_SCALED) acc *= P.bscale;
+        T g0 = cur.g[0][j], g1 = cur.g[1][j], g2 = cur.g[2][j];
+        if (!OM1) {
+          g0 *= om;
+          g1 *= om;
+          g2 *= om;
+        }
+        if (xq >= 1) acc = fma(-g0, xp, acc);
+        if (has_y) acc = fma(-g1, sh, acc);
+        if (has_in) acc = fma(-g2, ring_in[(s % WV_R) * 32 + lane], acc);
+        v = acc;
+        if (act) P.xnew[gi0 + xq * dgi] = acc;
+      }
+      if (act) xp = v;
+      if (has_out) ring_out[(s % WV_R) * 32 + lane] = v;
+    }
+    if (has_out) mb_arrive(&full[wz * NS + st]);
+    if (has_in) mb_arrive(&empty[(wz - 1) * NS + st]);
+  }
+}
+
 // Decomposed ILU(0) pivots (fp64): d_i = a_ii - sum over upstream cells j of
 // the same subdomain of a_ij a_ji / d_j.
 template <class T, class TC>
@@ -665,6 +812,21 @@ ndiag_status run3d(Handle* h, const GP<T, TC>& P, unsigned nsub, size_t smem, do
   ++h->launches;
   if (bytes > 0) ++h->sweep_launches;
   if constexpr (KIND != KIND_SOR) {
+    if (pencil && wave_fits(P) && h->w3_wave) {
+      const int nw = P.sp[2].len(0);
+      const size_t sm = sizeof(T) * (size_t)nw * WvCfg<T>::R * 32 +
+                        sizeof(unsigned long long) * 2 * nw * WvCfg<T>::NS;
+      static bool wattr = false;
+      if (!wattr) {
+        ND_CUDA(cudaFuncSetAttribute(sweep3d_wave_kernel<T, TC, KIND, OM1>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        wattr = true;
+      }
+      sweep3d_wave_kernel<T, TC, KIND, OM1><<<nsub, 32 * nw, sm, h->stream>>>(P);
+      ND_CUDA(cudaGetLastError());
+      prof_end(h, slot, bytes);
+      return NDIAG_OK;
+    }
     if (pencil) {
       sweep3d_pencil_kernel<T, TC, KIND, OM1><<<nsub, GT, 2 * sizeof(T) * (size_t)pencil_rows(P), h->stream>>>(P);
       ND_CUDA(cudaGetLastError());
@@ -685,6 +847,11 @@ ndiag_status run3d(Handle* h, const GP<T, TC>& P, unsigned nsub, size_t smem, do
 template <class T, class TC>
 int pencil_rows(const GP<T, TC>& P) {
   return P.sp[1].len(0) * P.sp[2].len(0);
+}
+// the wavefront walk: a lane per row along y and a warp per plane along z
+template <class T, class TC>
+bool wave_fits(const GP<T, TC>& P) {
+  return P.sp[1].len(0) <= 32 && P.sp[2].len(0) <= 32;
 }
 
 // Level-ordered copy of a scaled set (7 arrays) in the frame of P (the

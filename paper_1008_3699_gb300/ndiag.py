@@ -30,7 +30,7 @@ PREC_NONE, PREC_SSOR, PREC_ILU0, PREC_MG = 0, 1, 2, 3
 EXPORTED = ["ndiag_set_allocator", "ndiag_last_error", "ndiag_create", "ndiag_destroy", "ndiag_cells",
             "ndiag_precision", "sor_sweep", "ssor_apply", "mg_apply", "ndiag_mg_levels", "ndiag_selftest_wait", "ilu0_factor", "ilu0_apply", "ndiag_residual",
             "krylov_solve", "ndiag_set_history", "ndiag_tune_omega", "ndiag_profile", "ndiag_read_counters", "ilu0_apply_noalloc",
-            "ndiag_set_sweep9_kernel",
+            "ndiag_set_wavefront",
             "ndiag_batch_create", "ndiag_batch_autotune", "ndiag_batch_tiles", "ndiag_batch_solve",
             "ndiag_batch_ssor_apply",
             "ndiag_batch_cells", "ndiag_batch_launches", "ndiag_batch_destroy",
@@ -115,7 +115,7 @@ def load(path: str = LIB_PATH):
     L.ndiag_set_history.argtypes = [P, P, I]
     L.ndiag_tune_omega.argtypes = [P, P, D, I, I, P, ctypes.POINTER(I)]
     L.ndiag_profile.argtypes = [P, I]
-    L.ndiag_set_sweep9_kernel.argtypes = [P, I]
+    L.ndiag_set_wavefront.argtypes = [P, I]
     L.ndiag_read_counters.argtypes = [P, ctypes.POINTER(Counters)]
     L.ndiag_batch_create.argtypes = [ctypes.POINTER(P), I, P, P, P, P, D, P]
     L.ndiag_batch_autotune.argtypes = [P, P]
@@ -257,9 +257,9 @@ class NDiag:
         _check(self.L, self.L.ndiag_residual(self.h, _ptr(b), _ptr(x), _ptr(r), ctypes.byref(nrm)))
         return nrm.value
 
-    def set_sweep9_kernel(self, wave=True):
-        """fp64 decomposed 9-point triangular sweeps: wavefront (True) or level kernel."""
-        _check(self.L, self.L.ndiag_set_sweep9_kernel(self.h, 1 if wave else 0))
+    def set_wavefront(self, on=True):
+        """Wavefront kernels (9-point fp64 triangular sweeps, 3D one-cell walks) or the level kernels."""
+        _check(self.L, self.L.ndiag_set_wavefront(self.h, 1 if on else 0))
 
     def profile(self, enable=True):
         """Reset the launch counters; with enable, time every sweep kernel."""

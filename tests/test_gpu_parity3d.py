@@ -201,3 +201,47 @@ def test_full_size_applies_match_oracle(nd):
     h32.ssor_apply(1.0, _t(r, torch.float32), z32)
     assert _rel(z32.cpu().numpy(), want) <= 2e-5
     h32.close()
+
+
+WAVE_CASES = [((12, 10, 9), (2, 2, 2)), ((13, 11, 7), (3, 2, 2)), ((5, 6, 7), (5, 3, 2)), ((64, 64, 64), (2, 2, 2)),
+              ((40, 33, 35), (1, 1, 1)), ((70, 20, 66), (2, 1, 2)), ((9, 40, 12), (1, 1, 1))]
+
+
+@pytest.mark.parametrize("n,sub", WAVE_CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_wavefront_walk3d_matches_the_level_walk_and_the_oracle(nd, n, sub, prec):
+    """The 3D one-cell walk as a wavefront (warp per plane, lane per row,
+    shared ring between planes) against the level walk (1e-13 fp64 / 1e-6
+    fp32) and the oracle (1e-12 / 2e-5): ILU(0) apply (forward and reverse
+    phase) and SSOR apply (forward and transposed passes), on uneven, one-cell
+    thick, one-subdomain and 32-plane subdomains; subdomains with more than 32
+    rows along y or z take the level walk."""
+    import torch
+    d = _nonsym7(n, 401 + sub[0])
+    ds = _sym7(n, 402 + sub[1])
+    N = n[0] * n[1] * n[2]
+    r = np.random.default_rng(403).uniform(-1, 1, N)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    tol_o, tol_k = (1e-12, 1e-13) if prec == "fp64" else (2e-5, 1e-6)
+    ref = oracle.Problem(3, n, 7, d, sub)
+    ref.ilu0_factor(oracle.DECOMPOSED)
+    want_ilu = ref.ilu0_apply(r)
+    want_ssor = oracle.Problem(3, n, 7, ds, sub).ssor_apply(oracle.DECOMPOSED, 1.0, r)
+    got = {}
+    for wave in (True, False):
+        h = nd.NDiag(3, n, 7, d, sub, prec)
+        h.set_wavefront(wave)
+        h.ilu0_factor(nd.DECOMPOSED)
+        z = _t(np.zeros(N), dt)
+        h.ilu0_apply(_t(r, dt), z)
+        h.close()
+        hs = nd.NDiag(3, n, 7, ds, sub, prec)
+        hs.set_wavefront(wave)
+        zs = _t(np.zeros(N), dt)
+        hs.ssor_apply(1.0, _t(r, dt), zs)
+        hs.close()
+        got[wave] = (z.cpu().numpy().astype(np.float64), zs.cpu().numpy().astype(np.float64))
+    assert _rel(got[True][0], want_ilu) <= tol_o
+    assert _rel(got[True][1], want_ssor) <= tol_o
+    assert _rel(got[True][0], got[False][0]) <= tol_k
+    assert _rel(got[True][1], got[False][1]) <= tol_k

@@ -259,7 +259,7 @@ def test_wavefront_sweeps9_match_the_oracle_and_the_level_kernel(nd, n, sub, fac
     out = {}
     for wave in (True, False):
         h = nd.NDiag(2, n, 9, d, sub, "fp64")
-        h.set_sweep9_kernel(wave)
+        h.set_wavefront(wave)
         h.ilu0_factor(mode_g)
         z = _t(np.zeros(N))
         for _ in range(2):  # the second apply reuses the packed copy
