@@ -244,27 +244,24 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
       } else {
         acc = __ldg(P.rhs + gi);
       }
-      // upstream neighbours: block partners, or earlier blocks' members
+      // upstream neighbours: block partners, or earlier blocks' members.
+      // Every load is issued without a branch (absent terms read the member's
+      // own cell and are dropped by a select), so that all of a block's loads
+      // can be in flight at once.
       partners(m, cm, gi, om);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int up = cm[a] ? 1 : 0;  // upstream side of the member along a
-        if (C >> a & 1) {
-          // the block partner along a (set by partners)
-        } else if (lc[a] >= 1) {
-          T g = ldco<T, TC>(cptr(P, a, up) + gi);
-          if (!OM1) g *= om;
-          const int64_t gp = gi + (up ? P.stride[a] : -P.stride[a]);
-          T v;
-          if (sub == 0) {
-            v = __ldcg(P.xnew + gp);
-          } else {
-            int pc[3] = {lc[0], lc[1], lc[2]};
-            pc[a] -= 1;
-            v = tw[TI.slot(sub, pc)];
-          }
-          acc = fma(-g, v, acc);
-        }
+        const bool use = !(C >> a & 1) && lc[a] >= 1;
+        T g = ldco<T, TC>(cptr(P, a, up) + gi);
+        if (!OM1) g *= om;
+        const int64_t gp = use ? gi + (up ? P.stride[a] : -P.stride[a]) : gi;
+        int pc[3] = {lc[0], lc[1], lc[2]};
+        pc[a] = use ? pc[a] - 1 : 0;
+        const T vg = __ldcg(P.xnew + gp);
+        const T vt = sub != 0 ? tw[TI.slot(sub, pc)] : T(0);
+        const T v = sub == 0 ? vg : vt;
+        acc = use ? fma(-g, v, acc) : acc;
       }
     } else {
       // transposed: dependents are the downstream neighbours inside the
@@ -286,24 +283,23 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
         } else {
           inside = lc[a] + 1 < S.len[a];
         }
-        if (!inside) continue;
+        // loads without a branch, as in the forward case
         T g = ldco<T, TC>(cptr(P, a, dn) + gi);
         if (!OM1) g *= om;
-        const int64_t gq = gi + (dn ? P.stride[a] : -P.stride[a]);
-        T v;
-        if (sub == 0 || twin_axis) {
-          v = __ldcg(P.xnew + gq);
-        } else {
-          // same twin subset one step downstream: this launch's store
-          // if that block is of the same kind, else an earlier launch
-          int pc[3] = {lc[0], lc[1], lc[2]};
-          pc[a] += 1;
-          int oc[3] = {own[0], own[1], own[2]};
-          oc[a] += 1;
-          const int C2 = ((oc[0] == 0) | ((oc[1] == 0) << 1) | ((oc[2] == 0) << 2)) & tcode;
-          v = (__popc(C2) == nC) ? tw[TI.slot(sub, pc)] : __ldcg(P.xnew + gq);
-        }
-        acc = fma(-g, v, acc);
+        const int64_t gq = inside ? gi + (dn ? P.stride[a] : -P.stride[a]) : gi;
+        // same twin subset one step downstream: this launch's store if that
+        // block is of the same kind, else an earlier launch
+        int pc[3] = {lc[0], lc[1], lc[2]};
+        pc[a] += 1;
+        int oc[3] = {own[0], own[1], own[2]};
+        oc[a] += 1;
+        const int C2 = ((oc[0] == 0) | ((oc[1] == 0) << 1) | ((oc[2] == 0) << 2)) & tcode;
+        const bool from_tw = inside && !(sub == 0 || twin_axis) && __popc(C2) == nC;
+        if (!from_tw) pc[0] = pc[1] = pc[2] = 0;
+        const T vg = __ldcg(P.xnew + gq);
+        const T vt = sub != 0 ? tw[TI.slot(sub, pc)] : T(0);
+        const T v = from_tw ? vt : vg;
+        acc = inside ? fma(-g, v, acc) : acc;
       }
     }
     hv[m] = acc;
