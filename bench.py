@@ -438,7 +438,7 @@ def extra_fp32_refine_3d(torch, nd, W, args, n):
            "outer": info["outer"], "relres": info["relres"], "ssor_apply_ms": apply_ms,
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                         "bytes_per_cell": bpc, "peak_kind": kind,
-                        "kernel": "fp32 SSOR apply (sweep3d block passes + pencil passes)"}}
+                        "kernel": "fp32 SSOR apply (sweep3d_kernel block passes + sweep3d_wave_kernel walks)"}}
     if not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -583,7 +583,7 @@ def workload_poisson3d(args):
         gbs = apply_bytes / (apply_ms / 1e3) / 1e9
         out[prec + "_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                                    "frac": gbs / peak, "peak_kind": kind,
-                                   "kernel": "SSOR apply (sweep3d_kernel block passes + sweep3d_pencil_kernel)"}
+                                   "kernel": "SSOR apply (sweep3d_kernel block passes + sweep3d_wave_kernel walks)"}
         out[prec] = {"ssor_apply_ms": apply_ms, "sweep_gcell_per_s": 2 * N / apply_ms / 1e6,
                      **{k: info[k] for k in ("iters", "outer", "relres", "wall_s")}}
         h.close()
@@ -699,7 +699,7 @@ def workload_serving(args):
                       "relres_max": max(r["relres"] for r, _ in res), "max_running": st["max_running"],
                       "ninept_ilu_apply_2048": {"ms": ms9, "roofline": {
                           "bound": "hbm", "achieved": gbs9, "peak": peak, "unit": "GB/s", "frac": gbs9 / peak,
-                          "peak_kind": kind, "kernel": "sweep9_kernel (ILU(0) forward and backward, fp64)"}}}))
+                          "peak_kind": kind, "kernel": "sweep9w_kernel (wavefront; ILU(0) forward and backward, fp64)"}}}))
 
 
 def workload_mg2048(args):

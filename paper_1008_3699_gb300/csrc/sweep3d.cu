@@ -29,6 +29,8 @@
 // The decomposed ILU(0) pivots follow d_i = a_ii - sum_{j in J_i, i not in J_j}
 // a_ij a_ji / d_j (Sec. 5); mutual pairs drop out, so only upstream cells of
 // the same subdomain enter and no twins are needed.
+#include <algorithm>
+
 #include "sweep_common.cuh"
 
 namespace nd {
@@ -380,7 +382,14 @@ __global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
     // Block regions: only cells with a zero coordinate can be blocks; cell c
     // of a level enumerates face a = c / umax (coordinate a = 0), the cell
     // taken on the first face where it has a zero coordinate.
-    const int nq = blocks_only ? 3 * umax : h * d;
+    // Block passes of subdomains up to 32 a side: warps 0..2 take the face
+    // cells of the x, y and z faces, lanes 0..2 of warp 3 the cells of the xy,
+    // xz and yz edges (and the corner). The cells of a face warp share one
+    // block solve with compile-time axes; the three edges share the solve
+    // with run-time axes, so their 4x4 systems run side by side instead of one
+    // after another.
+    const bool split = blocks_only && umax <= 32;
+    const int nq = split ? 4 * 32 : blocks_only ? 3 * umax : h * d;
     for (int q = threadIdx.x; q < nq; q += blockDim.x) {
       int x, y, z;
       if (!blocks_only) {
@@ -388,8 +397,17 @@ __global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
         z = q / h;
         x = L - y - z;
         if (x < 0 || x >= w) continue;
+      } else if (split && q >= 3 * 32) {
+        const int e = q - 3 * 32;
+        if (e >= 3 || (L == 0 && e > 0)) continue;
+        x = e == 2 ? L : 0;
+        y = e == 1 ? L : 0;
+        z = e == 0 ? L : 0;
+        if (x >= w || y >= h || z >= d) continue;
+        const int Ce = ((x == 0) | ((y == 0) << 1) | ((z == 0) << 2)) & tcode;
+        if (__popc(Ce) < 2) continue;  // a face cell (its face warp takes it) or none
       } else {
-        const int a = q / umax, u = q - a * umax;
+        const int a = split ? q >> 5 : q / umax, u = split ? q & 31 : q - a * umax;
         const int lu = a == 0 ? h : w, lv = a == 2 ? h : d;
         const int v = L - u;
         if (u >= lu || v < 0 || v >= lv) continue;
@@ -402,6 +420,7 @@ __global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
           x = u, y = v, z = 0;
           if (x == 0 || y == 0) continue;
         }
+        if (split && __popc(((x == 0) | ((y == 0) << 1) | ((z == 0) << 2)) & tcode) >= 2) continue;  // an edge warp's
       }
       const int own[3] = {x, y, z};
       const int C = ((x == 0) | ((y == 0) << 1) | ((z == 0) << 2)) & tcode;
@@ -455,6 +474,10 @@ __global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
           }
         }
         P.xnew[gi] = acc;
+        continue;
+      }
+      if (split && __popc(C) == 2) {  // the edge warp: one code path for the three edges
+        block_solve<T, TC, KIND, OM1, 2>(P, S, TI, tw, x, y, z, C, tcode);
         continue;
       }
       if constexpr (sizeof(T) == 4) {
