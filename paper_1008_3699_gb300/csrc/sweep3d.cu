@@ -358,8 +358,21 @@ __device__ __noinline__ void corner_block(const GP<T, TC>& P, const Sub& S, cons
   block_solve<T, TC, KIND, OM1, 3>(P, S, TI, tw, x, y, z, C, tcode);
 }
 
+// the 8x8 corner of the 4-byte variants out of line in the six-warp block
+// kernel, so that it does not set that kernel's register budget
 template <class T, class TC, int KIND, bool OM1>
-__global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
+__device__ __noinline__ void corner_block_cm(const GP<T, TC>& P, const Sub& S, const TwinIdx& TI, T* tw, int x,
+                                             int y, int z, int C, int tcode) {
+  block_solve<T, TC, KIND, OM1, 3, 7>(P, S, TI, tw, x, y, z, C, tcode);
+}
+
+// One level walk of a subdomain. SIX: the block passes of subdomains up to 32
+// a side in six warps (4-byte variants): warps 0..2 take the cells of the x,
+// y and z faces, lane 0 of warps 3..5 those of the xy, xz and yz edges (warp
+// 3 also the corner). Every warp then runs one block solve with compile-time
+// axes, and the three edges' 4x4 systems run side by side.
+template <class T, class TC, int KIND, bool OM1, bool SIX>
+__device__ __forceinline__ void sweep3d_body(const GP<T, TC>& P) {
   extern __shared__ __align__(16) unsigned char gsm[];
   T* tw = reinterpret_cast<T*>(gsm);
   const Sub S = subdomain(P, blockIdx.x);
@@ -382,14 +395,11 @@ __global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
     // Block regions: only cells with a zero coordinate can be blocks; cell c
     // of a level enumerates face a = c / umax (coordinate a = 0), the cell
     // taken on the first face where it has a zero coordinate.
-    // Block passes of subdomains up to 32 a side: warps 0..2 take the face
-    // cells of the x, y and z faces, lanes 0..2 of warp 3 the cells of the xy,
-    // xz and yz edges (and the corner). The cells of a face warp share one
-    // block solve with compile-time axes; the three edges share the solve
-    // with run-time axes, so their 4x4 systems run side by side instead of one
-    // after another.
-    const bool split = blocks_only && umax <= 32;
-    const int nq = split ? 4 * 32 : blocks_only ? 3 * umax : h * d;
+    // Without SIX (8-byte variants, 4 warps): warps 0..2 the faces, lanes
+    // 0..2 of warp 3 the edges, through the solve with run-time axes (one
+    // code path, so the three edges still run side by side).
+    const bool split = SIX || (blocks_only && umax <= 32);
+    const int nq = SIX ? 6 * 32 : split ? 4 * 32 : blocks_only ? 3 * umax : h * d;
     for (int q = threadIdx.x; q < nq; q += blockDim.x) {
       int x, y, z;
       if (!blocks_only) {
@@ -398,8 +408,8 @@ __global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
         x = L - y - z;
         if (x < 0 || x >= w) continue;
       } else if (split && q >= 3 * 32) {
-        const int e = q - 3 * 32;
-        if (e >= 3 || (L == 0 && e > 0)) continue;
+        const int e = SIX ? (q - 3 * 32) >> 5 : q - 3 * 32;
+        if ((SIX && (q & 31) != 0) || e >= 3 || (L == 0 && e > 0)) continue;
         x = e == 2 ? L : 0;
         y = e == 1 ? L : 0;
         z = e == 0 ? L : 0;
@@ -476,7 +486,12 @@ __global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
         P.xnew[gi] = acc;
         continue;
       }
-      if (split && __popc(C) == 2) {  // the edge warp: one code path for the three edges
+      if (SIX && __popc(C) == 3) {
+        if constexpr (sizeof(T) == 4) corner_block_cm<T, TC, KIND, OM1>(P, S, TI, tw, x, y, z, C, tcode);
+        else corner_block<T, TC, KIND, OM1>(P, S, TI, tw, x, y, z, C, tcode);
+        continue;
+      }
+      if (!SIX && split && __popc(C) == 2) {  // the edge warp: one code path for the three edges
         block_solve<T, TC, KIND, OM1, 2>(P, S, TI, tw, x, y, z, C, tcode);
         continue;
       }
@@ -498,6 +513,16 @@ __global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
     }
     __syncthreads();
   }
+}
+
+template <class T, class TC, int KIND, bool OM1>
+__global__ void __launch_bounds__(GT, 2) sweep3d_kernel(GP<T, TC> P) {
+  sweep3d_body<T, TC, KIND, OM1, false>(P);
+}
+
+template <class T, class TC, int KIND, bool OM1>
+__global__ void __launch_bounds__(6 * 32, 4) sweep3d_blocks_kernel(GP<T, TC> P) {
+  sweep3d_body<T, TC, KIND, OM1, true>(P);
 }
 
 // Pencil form of the level walk over the cells of one-cell blocks (C = 0) for
@@ -856,7 +881,18 @@ ndiag_status run3d(Handle* h, const GP<T, TC>& P, unsigned nsub, size_t smem, do
   // the block passes have at most 3 x (largest side) cells per level: half
   // the threads, so four CTAs fit an SM with up to 128 registers each
   const bool blocks = P.region != REG_ALL && P.region != REG_INTERIOR;
-  sweep3d_kernel<T, TC, KIND, OM1><<<nsub, blocks ? GT / 2 : GT, smem, h->stream>>>(P);
+  const int umax = std::max(P.sp[0].len(0), std::max(P.sp[1].len(0), P.sp[2].len(0)));
+  if (blocks && umax <= 32 && sizeof(T) == 4) {  // the 8-byte variants spill under the six-warp budget
+    static bool battr = false;
+    if (!battr) {
+      ND_CUDA(cudaFuncSetAttribute(sweep3d_blocks_kernel<T, TC, KIND, OM1>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      battr = true;
+    }
+    sweep3d_blocks_kernel<T, TC, KIND, OM1><<<nsub, 6 * 32, smem, h->stream>>>(P);
+  } else {
+    sweep3d_kernel<T, TC, KIND, OM1><<<nsub, blocks ? GT / 2 : GT, smem, h->stream>>>(P);
+  }
   ND_CUDA(cudaGetLastError());
   prof_end(h, slot, bytes);
   return NDIAG_OK;
