@@ -92,9 +92,11 @@ struct ProfRec {
 
 struct Multigrid;  // mg.cu
 
-// Packed copy of a scaled set for the 9-point wavefront sweeps (sweep9w.cu):
-// one per phase and kind, rebuilt when the set or the partition changes.
-struct W9Pack {
+// A kernel's private copy of a scaled set in its own operand order (the
+// 9-point wavefront sweeps, sweep9w.cu; the 3D forward block records,
+// sweep3d.cu): one per phase and kind, rebuilt when the set or the partition
+// changes.
+struct PackCache {
   const void* set_base = nullptr;
   unsigned set_version = 0;
   int64_t t = -1;
@@ -153,7 +155,8 @@ struct Handle {
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> ev_pool;
   Multigrid* mg = nullptr;       // V-cycle hierarchy (built on the first multigrid apply)
-  std::vector<W9Pack> w9pack;    // 9-point wavefront operands (sweep9w.cu)
+  std::vector<PackCache> w9pack; // 9-point wavefront operands (sweep9w.cu)
+  std::vector<PackCache> brec3d; // 3D forward block records (sweep3d.cu)
   bool w9_wave = true;           // 9-point wavefront sweeps where they apply
   bool w3_wave = true;           // 3D wavefront pencil walks where they apply
 };
@@ -252,7 +255,7 @@ ndiag_status launch_ilu_factor9_into(Handle* h, int mode, double* out);
 // (sweep9w.cu); NDIAG_EINVAL, with nothing launched, outside its cover
 ndiag_status launch_sweep9w(Handle* h, int kind, int mode, int64_t t, const ScaledSet& set, const void* rhs,
                             void* xnew);
-void w9pack_free(Handle* h);
+void w9pack_free(Handle* h);  // frees the 9-point operand copies and the 3D block records
 ndiag_status build_scaled_transposed(Handle* h, ScaledSet& set);
 
 // BLAS-1 and SpMV (blas.cu)

@@ -61,6 +61,9 @@ struct GP {  // 3D only (dim == 3)
   T bscale;
   DevStatus* st;
   int twin_slots;  // elements of the twin store
+  // forward block records (or null): record q of subdomain s at brec[s * twin_slots + q],
+  // q = the twin-store slot of the block's own cell on its first coupled face
+  const void* brec;
   // level-ordered copy of the scaled set (or null): array k of subdomain s at
   // level L and row q = y + h0 z of the reference frame is
   // lev[k * lev_arr + s * lev_sub + L * lev_hd0 + q]; lev_flip = axes on which
@@ -350,6 +353,180 @@ __device__ __forceinline__ T block_solve(const GP<T, TC>& P, const Sub& S, const
   return own_x;
 }
 
+// Record of one coupled face or edge block (2 or 4 members) of a forward
+// pass, in the members' canonical order: everything of block_solve's forward
+// branch that depends neither on the right-hand side nor on new values --
+// member cells, pivots, the upstream couplings and where their values come
+// from, and the inverse of the block matrix (Gauss-Jordan in the canonical
+// order, so that every CTA solving the block holds the same inverse). A solve
+// is then a gather and a small matrix-vector product.
+constexpr int64_t BREC_NONE = INT64_MIN;
+
+template <class T>
+struct BRec {
+  int64_t gi[4];      // member cells
+  int64_t src[4][3];  // upstream value: >= 0 a cell of xnew, < 0 the twin slot -1 - src, BREC_NONE absent
+  T inv[4];
+  T g[4][3];          // upstream couplings (0 where absent)
+  T minv[16];         // n x n, row-major
+  int dst[4];         // -1: the own member (to xnew), else its twin slot
+  int n, own;
+};
+
+template <class T, class TC, int KIND, int NC>
+__device__ void block_record(const GP<T, TC>& P, const Sub& S, const TwinIdx& TI, int x, int y, int z, int C,
+                             BRec<T>& R) {
+  const int own[3] = {x, y, z};
+  int axes[3] = {0, 0, 0}, nC = 0;
+  for (int a = 0; a < 3; ++a)
+    if (C >> a & 1) axes[nC++] = a;
+  constexpr int n = 1 << NC;
+  int mo = 0;
+  for (int r = 0; r < NC; ++r)
+    if (S.c[axes[r]] == 0) mo |= 1 << r;
+  double M[n][n];
+  R.n = n;
+  R.own = mo;
+  for (int m = 0; m < n; ++m) {
+    int lc[3] = {own[0], own[1], own[2]}, sub = 0;
+    for (int r = 0; r < NC; ++r)
+      if (((m ^ mo) >> r) & 1) {
+        lc[axes[r]] = -1;
+        sub |= 1 << axes[r];
+      }
+    int cm[3];
+    for (int a = 0; a < 3; ++a) cm[a] = S.c[a] ^ ((sub >> a) & 1);
+    int64_t gi = 0;
+    for (int a = 0; a < 3; ++a) gi += (int64_t)S.gco(a, lc[a]) * P.stride[a];
+    R.gi[m] = gi;
+    R.inv[m] = KIND == KIND_TRI_SCALED ? ldco<T, TC>(P.inv + gi) : T(0);
+    R.dst[m] = sub == 0 ? -1 : TI.slot(sub, lc);
+    for (int k = 0; k < n; ++k) M[m][k] = k == m ? 1.0 : 0.0;
+    for (int r = 0; r < NC; ++r) {
+      const int a = axes[r];
+      M[m][m ^ (1 << r)] = (double)ldco<T, TC>(cptr(P, a, cm[a] ? 1 : 0) + gi);
+    }
+    for (int a = 0; a < 3; ++a) {
+      const int up = cm[a] ? 1 : 0;
+      const bool use = !(C >> a & 1) && lc[a] >= 1;
+      R.g[m][a] = use ? ldco<T, TC>(cptr(P, a, up) + gi) : T(0);
+      if (!use) {
+        R.src[m][a] = BREC_NONE;
+      } else if (sub == 0) {
+        R.src[m][a] = gi + (up ? P.stride[a] : -P.stride[a]);
+      } else {
+        int pc[3] = {lc[0], lc[1], lc[2]};
+        pc[a] -= 1;
+        R.src[m][a] = -1 - (int64_t)TI.slot(sub, pc);
+      }
+    }
+  }
+  for (int m = n; m < 4; ++m) {
+    R.gi[m] = R.gi[0];
+    R.inv[m] = T(0);
+    R.dst[m] = -1;
+    for (int a = 0; a < 3; ++a) {
+      R.g[m][a] = T(0);
+      R.src[m][a] = BREC_NONE;
+    }
+  }
+  // inverse by Gauss-Jordan (diagonally dominant: no pivoting), in fp64
+  double I[n][n];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) I[i][j] = i == j ? 1.0 : 0.0;
+  for (int k = 0; k < n; ++k) {
+    const double r = 1.0 / M[k][k];
+    for (int j = 0; j < n; ++j) {
+      M[k][j] *= r;
+      I[k][j] *= r;
+    }
+    for (int i = 0; i < n; ++i) {
+      if (i == k) continue;
+      const double f = M[i][k];
+      for (int j = 0; j < n; ++j) {
+        M[i][j] = fma(-f, M[k][j], M[i][j]);
+        I[i][j] = fma(-f, I[k][j], I[i][j]);
+      }
+    }
+  }
+  for (int i = 0; i < 16; ++i) R.minv[i] = T(0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) R.minv[i * n + j] = (T)I[i][j];
+}
+
+// The forward solve of a recorded block: h_m = pivot r - sum of the upstream
+// terms (in the order of block_solve), x = Minv h; the own member to xnew, the
+// twins to the twin store.
+template <class T, class TC, int KIND, int N>
+__device__ __forceinline__ void block_solve_rec(const GP<T, TC>& P, const BRec<T>* __restrict__ R, T* tw) {
+  T hv[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) {
+    const int64_t gi = __ldg(&R->gi[m]);
+    const T rr = __ldg(P.rhs + gi);
+    T acc = KIND == KIND_TRI_SCALED ? __ldg(&R->inv[m]) * rr : rr;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      // absent terms read the member's own cell and are dropped by a select
+      // (that value may be anything, even not a number)
+      const int64_t sr = __ldg(&R->src[m][a]);
+      const bool use = sr != BREC_NONE;
+      const int64_t sc = use ? sr : gi;
+      const T vg = __ldcg(P.xnew + (sc >= 0 ? sc : gi));
+      const T vt = tw[sc >= 0 ? 0 : (int)(-1 - sc)];
+      const T v = sc >= 0 ? vg : vt;
+      acc = use ? fma(-__ldg(&R->g[m][a]), v, acc) : acc;
+    }
+    hv[m] = acc;
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T xs = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) xs = fma(__ldg(&R->minv[i * N + j]), hv[j], xs);
+    const int dd = __ldg(&R->dst[i]);
+    if (dd < 0) P.xnew[__ldg(&R->gi[i])] = xs;
+    else tw[dd] = xs;
+  }
+}
+
+// Builds the forward block records of one phase: one thread per (subdomain,
+// twin-store slot); slots that hold no face or edge block of the forward pass
+// get n = 0.
+template <class T, class TC, int KIND>
+__global__ void block_record_kernel(GP<T, TC> P, BRec<T>* out, int64_t total) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned sb = (unsigned)(q / P.twin_slots);
+    const int slot = (int)(q % P.twin_slots);
+    const Sub S = subdomain(P, sb);
+    const int w = S.len[0], h = S.len[1], d = S.len[2];
+    const TwinIdx TI = twin_index(w, h, d);
+    const int tcode = S.t[0] | (S.t[1] << 1) | (S.t[2] << 2);
+    BRec<T> R;
+    R.n = 0;
+    int x = -1, y = -1, z = -1, a = -1;
+    if (slot < TI.off[2]) {
+      a = 0, x = 0, y = slot / d, z = slot % d;
+    } else if (slot < TI.off[4]) {
+      a = 1, y = 0, x = (slot - TI.off[2]) / d, z = (slot - TI.off[2]) % d;
+    } else if (slot < TI.off[3]) {
+      a = 2, z = 0, x = (slot - TI.off[4]) / h, y = (slot - TI.off[4]) % h;
+    }
+    if (a >= 0 && x < w && y < h && z < d) {
+      const int own[3] = {x, y, z};
+      const int C = ((x == 0) | ((y == 0) << 1) | ((z == 0) << 2)) & tcode;
+      int first = -1;
+      for (int b = 0; b < 3; ++b)
+        if (first < 0 && ((C >> b) & 1) && own[b] == 0) first = b;
+      if (first == a) {
+        if (__popc(C) == 1) block_record<T, TC, KIND, 1>(P, S, TI, x, y, z, C, R);
+        else if (__popc(C) == 2) block_record<T, TC, KIND, 2>(P, S, TI, x, y, z, C, R);
+      }
+    }
+    out[q] = R;
+  }
+}
+
 // the 8x8 corner block (one per subdomain) of the fp64 variants out of line,
 // so that its registers do not weigh on the face and edge blocks
 template <class T, class TC, int KIND, bool OM1>
@@ -484,6 +661,14 @@ __device__ __forceinline__ void sweep3d_body(const GP<T, TC>& P) {
           }
         }
         P.xnew[gi] = acc;
+        continue;
+      }
+      if (P.brec && !P.transposed && (__popc(C) == 1 || __popc(C) == 2)) {  // a recorded block
+        const int f = (own[0] == 0 && (C & 1)) ? 0 : ((own[1] == 0 && (C & 2)) ? 1 : 2);
+        const BRec<T>* R = reinterpret_cast<const BRec<T>*>(P.brec) + (int64_t)blockIdx.x * P.twin_slots +
+                           TI.slot(1 << f, own);
+        if (__popc(C) == 1) block_solve_rec<T, TC, KIND, 2>(P, R, tw);
+        else block_solve_rec<T, TC, KIND, 4>(P, R, tw);
         continue;
       }
       if (SIX && __popc(C) == 3) {
@@ -882,7 +1067,10 @@ ndiag_status run3d(Handle* h, const GP<T, TC>& P, unsigned nsub, size_t smem, do
   // the threads, so four CTAs fit an SM with up to 128 registers each
   const bool blocks = P.region != REG_ALL && P.region != REG_INTERIOR;
   const int umax = std::max(P.sp[0].len(0), std::max(P.sp[1].len(0), P.sp[2].len(0)));
-  if (blocks && umax <= 32 && sizeof(T) == 4) {  // the 8-byte variants spill under the six-warp budget
+  // the six-warp layout for the 4-byte passes that solve their blocks themselves (the
+  // transposed passes; a forward pass with records runs four warps); the 8-byte
+  // variants spill under the six-warp budget
+  if (blocks && umax <= 32 && sizeof(T) == 4 && !P.brec) {
     static bool battr = false;
     if (!battr) {
       ND_CUDA(cudaFuncSetAttribute(sweep3d_blocks_kernel<T, TC, KIND, OM1>,
@@ -965,6 +1153,51 @@ ndiag_status attach_levels(Handle* h, ScaledSet& set, GP<T, TC>& P, int mode) {
   return NDIAG_OK;
 }
 
+// The forward block records of (set, phase, kind, partition), built on first
+// use and rebuilt when the set's values change; P.brec stays null when there
+// is no room (the block solves then gather their operands themselves).
+template <class T, class TC>
+ndiag_status attach_records(Handle* h, const ScaledSet& set, GP<T, TC>& P, int kind) {
+  P.brec = nullptr;
+  const int64_t nsub = (int64_t)P.sp[0].p * P.sp[1].p * P.sp[2].p;
+  const int64_t total = nsub * P.twin_slots;
+  const size_t bytes = sizeof(BRec<T>) * (size_t)total;
+  const int s0 = P.sp[0].p, s1 = P.sp[1].p * 65536 + P.sp[2].p;
+  PackCache* pc = nullptr;
+  for (PackCache& c : h->brec3d)
+    if (c.t == P.base && c.kind == kind && c.sub0 == s0 && c.sub1 == s1) pc = &c;
+  if (!pc) {
+    h->brec3d.push_back(PackCache{});
+    pc = &h->brec3d.back();
+    pc->t = P.base;
+    pc->kind = kind;
+    pc->sub0 = s0;
+    pc->sub1 = s1;
+  }
+  if (!pc->buf || pc->bytes != bytes || pc->set_base != set.base || pc->set_version != set.version) {
+    if (pc->bytes != bytes) {
+      dev_free(pc->buf, pc->bytes, h->stream);
+      pc->buf = (double*)dev_alloc(bytes, h->stream);
+      pc->bytes = pc->buf ? bytes : 0;
+    }
+    if (!pc->buf) {
+      pc->set_base = nullptr;
+      return NDIAG_OK;
+    }
+    const unsigned grid = (unsigned)std::min<int64_t>((total + 127) / 128, (int64_t)h->sm_count * 16);
+    ++h->launches;
+    if (kind == KIND_TRI_SCALED)
+      block_record_kernel<T, TC, KIND_TRI_SCALED><<<grid, 128, 0, h->stream>>>(P, (BRec<T>*)pc->buf, total);
+    else
+      block_record_kernel<T, TC, KIND_TRI_UNIT><<<grid, 128, 0, h->stream>>>(P, (BRec<T>*)pc->buf, total);
+    ND_CUDA(cudaGetLastError());
+    pc->set_base = set.base;
+    pc->set_version = set.version;
+  }
+  P.brec = pc->buf;
+  return NDIAG_OK;
+}
+
 template <class T, class TC>
 GP<T, TC> params(Handle* h, int mode, int64_t t, const ScaledSet& set, const void* rhs, const void* xold,
                  void* xnew, size_t& smem, unsigned& nsub) {
@@ -1044,7 +1277,9 @@ ndiag_status sweep3d_t(Handle* h, int kind, int mode, int64_t t, const double* o
       if (P.coupled) {  // the coupled blocks first, then the one-cell blocks
         P.region = REG_BLOCKS;
         b_now = 0.0;
+        if (om1 && h->w3_wave) ND_TRY(attach_records(h, set, P, decltype(kt)::value));
         ND_TRY(om1 ? go(kt, BT()) : go(kt, BF()));
+        P.brec = nullptr;
       }
       P.region = REG_INTERIOR;
       b_now = bytes;

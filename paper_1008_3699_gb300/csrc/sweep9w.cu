@@ -505,11 +505,11 @@ ndiag_status launch_sweep9w(Handle* h, int kind, int mode, int64_t t, const Scal
   P.st = h->status;
   const int na = kind == KIND_TRI_SCALED ? 5 : 4;
   // the packed copy of this set, phase and kind (rebuilt when the set changes)
-  W9Pack* pc = nullptr;
-  for (W9Pack& c : h->w9pack)
+  PackCache* pc = nullptr;
+  for (PackCache& c : h->w9pack)
     if (c.t == t && c.kind == kind) pc = &c;
   if (!pc) {
-    h->w9pack.push_back(W9Pack{});
+    h->w9pack.push_back(PackCache{});
     pc = &h->w9pack.back();
     pc->t = t;
     pc->kind = kind;
@@ -575,11 +575,13 @@ ndiag_status launch_sweep9w(Handle* h, int kind, int mode, int64_t t, const Scal
 }
 
 void w9pack_free(Handle* h) {
-  for (W9Pack& c : h->w9pack) {
+  for (PackCache& c : h->w9pack) {
     dev_free(c.buf, c.bytes, h->stream);
     dev_free(c.rdx, c.rdx_bytes, h->stream);
   }
   h->w9pack.clear();
+  for (PackCache& c : h->brec3d) dev_free(c.buf, c.bytes, h->stream);
+  h->brec3d.clear();
 }
 
 }  // namespace nd
