@@ -373,9 +373,9 @@ struct BRec {
   int n, own;
 };
 
-template <class T, class TC, int KIND, int NC>
+template <class T, class TC, int KIND, int NC, bool TR>
 __device__ void block_record(const GP<T, TC>& P, const Sub& S, const TwinIdx& TI, int x, int y, int z, int C,
-                             BRec<T>& R) {
+                             int tcode, BRec<T>& R) {
   const int own[3] = {x, y, z};
   int axes[3] = {0, 0, 0}, nC = 0;
   for (int a = 0; a < 3; ++a)
@@ -399,7 +399,7 @@ __device__ void block_record(const GP<T, TC>& P, const Sub& S, const TwinIdx& TI
     int64_t gi = 0;
     for (int a = 0; a < 3; ++a) gi += (int64_t)S.gco(a, lc[a]) * P.stride[a];
     R.gi[m] = gi;
-    R.inv[m] = KIND == KIND_TRI_SCALED ? ldco<T, TC>(P.inv + gi) : T(0);
+    R.inv[m] = (!TR && KIND == KIND_TRI_SCALED) ? ldco<T, TC>(P.inv + gi) : T(0);
     R.dst[m] = sub == 0 ? -1 : TI.slot(sub, lc);
     for (int k = 0; k < n; ++k) M[m][k] = k == m ? 1.0 : 0.0;
     for (int r = 0; r < NC; ++r) {
@@ -408,16 +408,43 @@ __device__ void block_record(const GP<T, TC>& P, const Sub& S, const TwinIdx& TI
     }
     for (int a = 0; a < 3; ++a) {
       const int up = cm[a] ? 1 : 0;
-      const bool use = !(C >> a & 1) && lc[a] >= 1;
-      R.g[m][a] = use ? ldco<T, TC>(cptr(P, a, up) + gi) : T(0);
-      if (!use) {
-        R.src[m][a] = BREC_NONE;
-      } else if (sub == 0) {
-        R.src[m][a] = gi + (up ? P.stride[a] : -P.stride[a]);
-      } else {
+      if (!TR) {  // upstream neighbours of the member (block_solve's forward branch)
+        const bool use = !(C >> a & 1) && lc[a] >= 1;
+        R.g[m][a] = use ? ldco<T, TC>(cptr(P, a, up) + gi) : T(0);
+        if (!use) {
+          R.src[m][a] = BREC_NONE;
+        } else if (sub == 0) {
+          R.src[m][a] = gi + (up ? P.stride[a] : -P.stride[a]);
+        } else {
+          int pc[3] = {lc[0], lc[1], lc[2]};
+          pc[a] -= 1;
+          R.src[m][a] = -1 - (int64_t)TI.slot(sub, pc);
+        }
+      } else {  // downstream dependents inside the member's subdomain (the transposed branch)
+        const int dn = 1 - up;
+        const bool twin_axis = (sub >> a) & 1;
+        const int gd = S.gco(a, lc[a]) + (dn ? 1 : -1);
+        bool inside;
+        if (twin_axis) {
+          const int it = S.c[a] ? S.idx[a] + 1 : S.idx[a] - 1;
+          const int t0 = P.sp[a].lo(it), t1 = t0 + P.sp[a].len(it);
+          inside = gd >= t0 && gd < t1;
+        } else {
+          inside = lc[a] + 1 < S.len[a];
+        }
+        R.g[m][a] = inside ? ldco<T, TC>(cptr(P, a, dn) + gi) : T(0);
+        if (!inside) {
+          R.src[m][a] = BREC_NONE;
+          continue;
+        }
+        const int64_t gq = gi + (dn ? P.stride[a] : -P.stride[a]);
         int pc[3] = {lc[0], lc[1], lc[2]};
-        pc[a] -= 1;
-        R.src[m][a] = -1 - (int64_t)TI.slot(sub, pc);
+        pc[a] += 1;
+        int oc[3] = {own[0], own[1], own[2]};
+        oc[a] += 1;
+        const int C2 = ((oc[0] == 0) | ((oc[1] == 0) << 1) | ((oc[2] == 0) << 2)) & tcode;
+        const bool from_tw = !(sub == 0 || twin_axis) && __popc(C2) == NC;
+        R.src[m][a] = from_tw ? -1 - (int64_t)TI.slot(sub, pc) : gq;
       }
     }
   }
@@ -493,7 +520,7 @@ __device__ __forceinline__ void block_solve_rec(const GP<T, TC>& P, const BRec<T
 // Builds the forward block records of one phase: one thread per (subdomain,
 // twin-store slot); slots that hold no face or edge block of the forward pass
 // get n = 0.
-template <class T, class TC, int KIND>
+template <class T, class TC, int KIND, bool TR>
 __global__ void block_record_kernel(GP<T, TC> P, BRec<T>* out, int64_t total) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     const unsigned sb = (unsigned)(q / P.twin_slots);
@@ -519,8 +546,8 @@ __global__ void block_record_kernel(GP<T, TC> P, BRec<T>* out, int64_t total) {
       for (int b = 0; b < 3; ++b)
         if (first < 0 && ((C >> b) & 1) && own[b] == 0) first = b;
       if (first == a) {
-        if (__popc(C) == 1) block_record<T, TC, KIND, 1>(P, S, TI, x, y, z, C, R);
-        else if (__popc(C) == 2) block_record<T, TC, KIND, 2>(P, S, TI, x, y, z, C, R);
+        if (__popc(C) == 1) block_record<T, TC, KIND, 1, TR>(P, S, TI, x, y, z, C, tcode, R);
+        else if (__popc(C) == 2) block_record<T, TC, KIND, 2, TR>(P, S, TI, x, y, z, C, tcode, R);
       }
     }
     out[q] = R;
@@ -663,7 +690,7 @@ __device__ __forceinline__ void sweep3d_body(const GP<T, TC>& P) {
         P.xnew[gi] = acc;
         continue;
       }
-      if (P.brec && !P.transposed && (__popc(C) == 1 || __popc(C) == 2)) {  // a recorded block
+      if (P.brec && (__popc(C) == 1 || __popc(C) == 2)) {  // a recorded block
         const int f = (own[0] == 0 && (C & 1)) ? 0 : ((own[1] == 0 && (C & 2)) ? 1 : 2);
         const BRec<T>* R = reinterpret_cast<const BRec<T>*>(P.brec) + (int64_t)blockIdx.x * P.twin_slots +
                            TI.slot(1 << f, own);
@@ -1159,18 +1186,20 @@ ndiag_status attach_levels(Handle* h, ScaledSet& set, GP<T, TC>& P, int mode) {
 template <class T, class TC>
 ndiag_status attach_records(Handle* h, const ScaledSet& set, GP<T, TC>& P, int kind) {
   P.brec = nullptr;
+  const bool tr = P.transposed != 0;
+  const int key = kind + (tr ? 16 : 0);
   const int64_t nsub = (int64_t)P.sp[0].p * P.sp[1].p * P.sp[2].p;
   const int64_t total = nsub * P.twin_slots;
   const size_t bytes = sizeof(BRec<T>) * (size_t)total;
   const int s0 = P.sp[0].p, s1 = P.sp[1].p * 65536 + P.sp[2].p;
   PackCache* pc = nullptr;
   for (PackCache& c : h->brec3d)
-    if (c.t == P.base && c.kind == kind && c.sub0 == s0 && c.sub1 == s1) pc = &c;
+    if (c.t == P.base && c.kind == key && c.sub0 == s0 && c.sub1 == s1) pc = &c;
   if (!pc) {
     h->brec3d.push_back(PackCache{});
     pc = &h->brec3d.back();
     pc->t = P.base;
-    pc->kind = kind;
+    pc->kind = key;
     pc->sub0 = s0;
     pc->sub1 = s1;
   }
@@ -1186,10 +1215,12 @@ ndiag_status attach_records(Handle* h, const ScaledSet& set, GP<T, TC>& P, int k
     }
     const unsigned grid = (unsigned)std::min<int64_t>((total + 127) / 128, (int64_t)h->sm_count * 16);
     ++h->launches;
-    if (kind == KIND_TRI_SCALED)
-      block_record_kernel<T, TC, KIND_TRI_SCALED><<<grid, 128, 0, h->stream>>>(P, (BRec<T>*)pc->buf, total);
+    if (tr)
+      block_record_kernel<T, TC, KIND_TRI_UNIT, true><<<grid, 128, 0, h->stream>>>(P, (BRec<T>*)pc->buf, total);
+    else if (kind == KIND_TRI_SCALED)
+      block_record_kernel<T, TC, KIND_TRI_SCALED, false><<<grid, 128, 0, h->stream>>>(P, (BRec<T>*)pc->buf, total);
     else
-      block_record_kernel<T, TC, KIND_TRI_UNIT><<<grid, 128, 0, h->stream>>>(P, (BRec<T>*)pc->buf, total);
+      block_record_kernel<T, TC, KIND_TRI_UNIT, false><<<grid, 128, 0, h->stream>>>(P, (BRec<T>*)pc->buf, total);
     ND_CUDA(cudaGetLastError());
     pc->set_base = set.base;
     pc->set_version = set.version;
@@ -1295,8 +1326,11 @@ ndiag_status sweep3d_t(Handle* h, int kind, int mode, int64_t t, const double* o
   for (int r = REG_INTERIOR; r <= last; ++r) {
     P.region = r;
     b_now = r == REG_INTERIOR ? bytes : 0.0;
+    // the face and edge passes solve recorded blocks (one record set for both)
+    if (r == REG_FACES && om1 && h->w3_wave && h->dim == 3) ND_TRY(attach_records(h, set, P, KIND_TRI_UNIT));
     ND_TRY(om1 ? go(S2(), BT()) : go(S2(), BF()));
   }
+  P.brec = nullptr;
   return NDIAG_OK;
 }
 
