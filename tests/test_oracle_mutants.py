@@ -13,6 +13,7 @@ import pytest
 import oracle
 from paper_1008_3699_gb300 import workloads as W
 from tests.oracle_dense import assemble, full_n, jmask_bool, neighbours
+from tests.test_oracle_ninepoint import face_sets_hold, reflected_blocks_hold
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.cpp")
 
@@ -235,6 +236,13 @@ MUTANTS = [
     ("lexicographic order reversed",
      "    if (kq != ki) return kq < ki;", "    if (kq != ki) return kq > ki;",
      [pin_table1_pgs2, pin_printed_systems]),
+    ("9-point diagonal across an interface taken as new when upstream",
+     "  if (nz != 1) return false;  // diagonal neighbour across an interface: old value",
+     "  if (nz != 1) return precedes(cq, ci, csi);",
+     [lambda L: face_sets_hold((13, 11), (3, 2), L), lambda L: reflected_blocks_hold((13, 11), (3, 2), L)]),
+    ("column-wise order inside a subdomain (same iterate for 5 points, not for 9)",
+     "  for (int a = 2; a >= 0; --a) {\n    int64_t kq", "  for (int a = 0; a < 3; ++a) {\n    int64_t kq",
+     [lambda L: reflected_blocks_hold((13, 11), (3, 2), L)]),
 ]
 
 
