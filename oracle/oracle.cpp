@@ -50,7 +50,8 @@
 // outside it: the face implicit sets equal the 5-point ones (pinned to the
 // printed systems), a 5-point matrix in 9-point storage sweeps as the 5-point
 // problem, and with cross-interface face couplings removed each subdomain is
-// natural SOR of its reflected block (dense solve).
+// natural SOR of its reflected block (dense solve). The 9-point D-ILU pivots
+// are pinned by D-ILU's definition, diag(M) = diag(A).
 
 #include <algorithm>
 #include <cmath>

@@ -126,6 +126,24 @@ def pin_ilu_pattern(L, mode):
     return np.max(np.abs((M - A)[A != 0])) <= 1e-12
 
 
+def pin_dilu9(L):
+    """9-point decomposed D-ILU: M = (D~ + L) D~^-1 (D~ + U) has A's diagonal."""
+    n = (13, 11, 1)
+    d = _rand_diags(n, 9, 51)
+    pb = oracle.Problem(2, n, 9, d, (3, 2), library=L)
+    try:
+        pb.ilu0_factor(oracle.DECOMPOSED)
+    except RuntimeError:
+        return False
+    dt = pb.ilu0_export()
+    tf = pb.fwd_phase()
+    Jf = jmask_bool(pb.plan_info(1, tf)[0], 9)
+    Jb = jmask_bool(pb.plan_info(1, tf ^ 1)[0], 9)
+    M = (np.diag(dt) + assemble(n, 9, d, Jf, False).toarray()) @ np.diag(1 / dt) @ \
+        (np.diag(dt) + assemble(n, 9, d, Jb, False).toarray())
+    A = assemble(n, 9, d).toarray()
+    return np.max(np.abs(np.diag(M) - np.diag(A))) <= 1e-14 * np.max(np.abs(np.diag(A)))
+
 def pin_krylov_counts(L, method):
     from tests.test_oracle_pins import krylov_counts_match_scipy
     try:
@@ -243,6 +261,10 @@ MUTANTS = [
     ("column-wise order inside a subdomain (same iterate for 5 points, not for 9)",
      "  for (int a = 2; a >= 0; --a) {\n    int64_t kq", "  for (int a = 0; a < 3; ++a) {\n    int64_t kq",
      [lambda L: reflected_blocks_hold((13, 11), (3, 2), L)]),
+    ("9-point D-ILU pivot sums the face neighbours only",
+     "          if (pl.jmask[j] >> kb & 1) continue;  // mutual pair: no elimination term",
+     "          if (pl.jmask[j] >> kb & 1) continue;  // mutual pair: no elimination term\n          if (k >= 5) continue;",
+     [pin_dilu9]),
 ]
 
 

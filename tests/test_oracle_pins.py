@@ -402,20 +402,28 @@ def test_decomposed_ilu0_reproduces_A_on_its_pattern(orc, dim, n, stencil, sub):
         assert np.allclose(pn.ilu0_export()[0], dt, rtol=1e-14, atol=0)
 
 
-def test_decomposed_ilu0_9pt_is_consistent(orc):
-    # parity unpinned for the 9-point decomposed factor; only M z = r holds
-    n = (10, 9, 1)
-    d = _random_diags(n, 9, 51)
-    pb = orc.Problem(2, n, 9, d, (2, 2))
+@pytest.mark.parametrize("n,sub", [((10, 9), (2, 2)), ((13, 11), (3, 2)), ((9, 7), (9, 1)), ((12, 9), (4, 3)),
+                                   ((7, 10), (1, 5)), ((10, 10), (1, 1))])
+def test_decomposed_ilu0_9pt_is_dilu(orc, n, sub):
+    # Reading 12 keeps A's off-diagonals in L and U and chooses the pivots so
+    # that M = (D~ + L) D~^-1 (D~ + U) has A's diagonal: the definition of
+    # D-ILU, which fixes every pivot once the upstream sets are fixed (those
+    # are pinned in test_oracle_ninepoint.py). Also M z = r for the apply.
+    fn = full_n(n)
+    N = int(np.prod(fn))
+    d = _random_diags(fn, 9, 51)
+    pb = orc.Problem(2, n, 9, d, sub)
     pb.ilu0_factor(orc.DECOMPOSED)
     dt = pb.ilu0_export()
     tf = pb.fwd_phase()
     Jf = jmask_bool(pb.plan_info(orc.DECOMPOSED, tf)[0], 9)
     Jb = jmask_bool(pb.plan_info(orc.DECOMPOSED, tf ^ 1)[0], 9)
-    Lj = assemble(n, 9, d, Jf, include_diag=False).toarray()
-    Uj = assemble(n, 9, d, Jb, include_diag=False).toarray()
+    Lj = assemble(fn, 9, d, Jf, include_diag=False).toarray()
+    Uj = assemble(fn, 9, d, Jb, include_diag=False).toarray()
     M = (np.diag(dt) + Lj) @ np.diag(1 / dt) @ (np.diag(dt) + Uj)
-    r = W.uniform_rhs(90, 2)
+    A = assemble(fn, 9, d).toarray()
+    assert np.max(np.abs(np.diag(M) - np.diag(A))) <= 1e-14 * np.max(np.abs(np.diag(A)))
+    r = W.uniform_rhs(N, 2)
     assert np.allclose(M @ pb.ilu0_apply(r), r, rtol=0, atol=1e-11)
 
 
