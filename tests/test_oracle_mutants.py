@@ -13,7 +13,7 @@ import pytest
 import oracle
 from paper_1008_3699_gb300 import workloads as W
 from tests.oracle_dense import assemble, full_n, jmask_bool, neighbours
-from tests.test_oracle_ninepoint import face_sets_hold, reflected_blocks_hold
+from tests.test_oracle_sweep_sets import face_sets_hold, reflected_blocks_hold
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.cpp")
 

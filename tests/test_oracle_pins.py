@@ -408,7 +408,7 @@ def test_decomposed_ilu0_9pt_is_dilu(orc, n, sub):
     # Reading 12 keeps A's off-diagonals in L and U and chooses the pivots so
     # that M = (D~ + L) D~^-1 (D~ + U) has A's diagonal: the definition of
     # D-ILU, which fixes every pivot once the upstream sets are fixed (those
-    # are pinned in test_oracle_ninepoint.py). Also M z = r for the apply.
+    # are pinned in test_oracle_sweep_sets.py). Also M z = r for the apply.
     fn = full_n(n)
     N = int(np.prod(fn))
     d = _random_diags(fn, 9, 51)

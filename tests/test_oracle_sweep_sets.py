@@ -1,6 +1,7 @@
-"""The oracle's decomposed 9-point sweep (Sec. 3 extends the method to the
-9-point stencil without details) pinned to computations outside its own code:
+"""The oracle's implicit sets where the paper prints no system to check them
+against, pinned to computations outside its own code.
 
+9-point sweep (Sec. 3 extends the method to it without details):
 - its implicit sets on the face neighbours are those of the 5-point sweep on
   the same grid and partition, which the printed coupled systems of Sec. 3-4
   pin; diagonal neighbours across an interface are never implicit;
@@ -11,6 +12,8 @@
   block, cells in lexicographic order of the frame reflected along the axes it
   sweeps backwards, with every neighbour outside it (diagonal ones included)
   at its old value: a dense solve with numpy.
+
+3D 7-point sweep (Sec. 4), all eight phases: the same per-subdomain reduction.
 """
 import numpy as np
 import pytest
@@ -126,3 +129,55 @@ def test_five_point_matrix_in_nine_point_storage_sweeps_as_five_point(orc, n, su
 @pytest.mark.parametrize("n,sub", PARTS)
 def test_subdomain_sweep_is_natural_sor_of_its_reflected_block(orc, n, sub):
     assert reflected_blocks_hold(n, sub)
+
+
+def _labels3(n, sub):
+    """Subdomain number of every cell of a 3D grid (equal split, the first
+    n mod p parts one longer)."""
+    cuts = []
+    for a in range(3):
+        q, r = divmod(n[a], sub[a])
+        cuts.append(np.repeat(np.arange(sub[a]), [q + (1 if k < r else 0) for k in range(sub[a])]))
+    N = n[0] * n[1] * n[2]
+    idx = np.arange(N)
+    x, y, z = idx % n[0], (idx // n[0]) % n[1], idx // (n[0] * n[1])
+    return cuts[0][x] + sub[0] * (cuts[1][y] + sub[1] * cuts[2][z]), (x, y, z)
+
+
+@pytest.mark.parametrize("n,sub", [((6, 5, 7), (2, 2, 3)), ((5, 4, 6), (5, 1, 2)), ((4, 6, 5), (1, 1, 1))])
+def test_3d_subdomain_sweep_is_natural_sor_of_its_reflected_block(orc, n, sub):
+    # Sec. 4: each subdomain sweeps from its start corner; with every coupling
+    # across an interface removed, its new values are natural (lexicographic
+    # z, y, x) SOR of its block in the frame reflected along the axes it
+    # sweeps backwards, with outside neighbours at their old values.
+    g = np.random.default_rng(41)
+    N = int(np.prod(n))
+    lab, (x, y, z) = _labels3(n, sub)
+    d = -g.uniform(0.1, 1.0, size=(7, N))
+    nb = neighbours(n, 7)
+    d[nb < 0] = 0.0
+    for k in range(1, 7):
+        across = (nb[k] >= 0) & (lab[np.maximum(nb[k], 0)] != lab)
+        d[k, across] = 0.0
+    d[0] = -d[1:].sum(axis=0) + g.uniform(0.05, 0.5, N)
+    pb = orc.Problem(3, n, 7, d, sub)
+    A = assemble(n, 7, d).toarray()
+    omega = g.uniform(0.6, 1.8, size=8)
+    b, u = g.uniform(-1, 1, N), g.uniform(-1, 1, N)
+    idx = np.arange(N)
+    for t in range(8):
+        got = pb.sor_sweep(orc.DECOMPOSED, t, omega, b, u)
+        _, corner, _, _ = pb.plan_info(orc.DECOMPOSED, t)
+        for s in np.unique(lab):
+            cells = idx[lab == s]
+            cs = int(corner[cells[0]])
+            assert (corner[cells] == cs).all()
+            keys = [-c[cells] if cs >> a & 1 else c[cells] for a, c in enumerate((x, y, z))]
+            order = cells[np.lexsort(keys)]
+            out = idx[lab != s]
+            As = A[np.ix_(order, order)]
+            r = b[order] - A[np.ix_(order, out)] @ u[out]
+            w = omega[cs]
+            D = np.diag(np.diag(As))
+            want = np.linalg.solve(D + w * np.tril(As, -1), ((1 - w) * D - w * np.triu(As, 1)) @ u[order] + w * r)
+            assert np.max(np.abs(got[order] - want)) <= 1e-12 * np.max(np.abs(want)), (t, s)
