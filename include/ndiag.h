@@ -7,6 +7,8 @@
  *
  * Conventions (all entry points):
  *  - Every call returns an ndiag_status and never aborts. NDIAG_OK = 0.
+ *  - Constructors (ndiag_create, ndiag_batch_create, ndiag_server_create,
+ *    eikonal_create) set *out to NULL first, so it is NULL after any failure.
  *  - Vectors are in natural cell order (x fastest, then y, then z).
  *  - "device" pointers are CUDA device pointers on the handle's device, owned
  *    by the caller; the library neither frees nor retains them after the call.

@@ -278,8 +278,9 @@ const char* ndiag_last_error(void) { return g_last_error.c_str(); }
 
 ndiag_status ndiag_create(ndiag** out, int dim, const int64_t n[3], int stencil, const double* diags,
                           const int sub[3], int precision, void* cuda_stream) {
-  if (!out || !n || !diags || !sub) return NDIAG_EINVAL;
+  if (!out) return NDIAG_EINVAL;
   *out = nullptr;
+  if (!n || !diags || !sub) return NDIAG_EINVAL;
   if (!((dim == 2 && (stencil == 5 || stencil == 9)) || (dim == 3 && stencil == 7))) {
     set_error("unsupported dim/stencil");
     return NDIAG_EINVAL;

@@ -571,8 +571,9 @@ extern "C" {
 
 ndiag_status ndiag_batch_create(ndiag_batch** out, int count, const int64_t* nx, const int64_t* ny,
                                 const double* const* diags, const int* tile, double omega, void* stream) {
-  if (!out || count < 1 || !nx || !ny || !diags || !(omega > 0.0 && omega < 2.0)) return NDIAG_EINVAL;
+  if (!out) return NDIAG_EINVAL;
   *out = nullptr;
+  if (count < 1 || !nx || !ny || !diags || !(omega > 0.0 && omega < 2.0)) return NDIAG_EINVAL;
   ndiag_batch* B = new ndiag_batch();
   B->np = count;
   B->omega = omega;

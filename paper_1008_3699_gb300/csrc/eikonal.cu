@@ -197,8 +197,9 @@ extern "C" {
 
 ndiag_status eikonal_create(ndiag_eik** out, const int64_t n[2], double h, const double* f, const int sub[2],
                             void* cuda_stream) {
-  if (!out || !n || !f || !sub || !(h > 0.0)) return NDIAG_EINVAL;
+  if (!out) return NDIAG_EINVAL;
   *out = nullptr;
+  if (!n || !f || !sub || !(h > 0.0)) return NDIAG_EINVAL;
   if (n[0] < 1 || n[1] < 1 || n[0] > (1 << 20) || n[1] > (1 << 20) || sub[0] < 1 || sub[1] < 1 ||
       sub[0] > n[0] || sub[1] > n[1]) {
     set_error("eikonal_create: bad sizes or subdomains");

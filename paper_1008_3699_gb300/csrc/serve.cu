@@ -158,8 +158,9 @@ void worker(ndiag_server* S) {
 extern "C" {
 
 ndiag_status ndiag_server_create(ndiag_server** out, int slots, size_t mem_budget) {
-  if (!out || slots < 1 || slots > 64) return NDIAG_EINVAL;
+  if (!out) return NDIAG_EINVAL;
   *out = nullptr;
+  if (slots < 1 || slots > 64) return NDIAG_EINVAL;
   ndiag_server* S = new ndiag_server();
   cudaGetDevice(&S->device);
   if (mem_budget == 0) {
