@@ -14,6 +14,7 @@ import oracle
 from paper_1008_3699_gb300 import workloads as W
 from tests.oracle_dense import assemble, full_n, jmask_bool, neighbours
 from tests.test_oracle_sweep_sets import face_sets_hold, reflected_blocks_hold
+from tests.test_oracle_tables6to8 import decomposed_within_table6
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.cpp")
 
@@ -204,7 +205,7 @@ def pin_full_apply(L):
 MUTANTS = [
     ("no interface coupling",
      "  return q_up_in_i && i_up_in_q;", "  return false;",
-     [pin_table1_pgs2, pin_printed_systems]),
+     [pin_table1_pgs2, pin_printed_systems, decomposed_within_table6]),
     ("1D starts outward",
      "  if (d == 1) return (int)(t & 1);", "  if (d == 1) return (int)((t + 1) & 1);",
      [pin_table1_pgs2]),
