@@ -86,7 +86,8 @@ const char* ndiag_last_error(void);
  * ndiag_create -- copy a structured n-diagonal matrix to the device and build
  * the partition and sweep schedule.
  *   dim       2 or 3.
- *   n         cells per axis, n[2] ignored when dim = 2; every n[a] >= 1.
+ *   n         cells per axis, n[2] ignored when dim = 2; 1 <= n[a] <= 2^20 and
+ *             N = the product of the n[a] below 2^31.
  *   stencil   5 (dim 2), 7 (dim 3) or 9 (dim 2).
  *   diags     HOST array, stencil * N doubles, diagonal-major (see above);
  *             read during the call only (the caller keeps ownership).
@@ -96,7 +97,9 @@ const char* ndiag_last_error(void);
  *   precision NDIAG_FP64, NDIAG_FP32 or NDIAG_FP32_D16 (the precision of the
  *             sweeps; residuals, dots and norms are always fp64).
  *   cuda_stream  cudaStream_t (NULL = legacy default stream).
- * Errors: NDIAG_EINVAL (sizes, stencil, diagonal <= 0), NDIAG_ENOMEM.
+ * Errors: NDIAG_EINVAL (a null pointer, dim/stencil, sizes, subdomain counts,
+ * precision, a diagonal entry that is not > 0, NaN included), NDIAG_ENOMEM,
+ * NDIAG_EDEVICE (no usable CUDA device).
  */
 ndiag_status ndiag_create(ndiag** out, int dim, const int64_t n[3], int stencil,
                           const double* diags, const int sub[3], int precision,
@@ -121,7 +124,8 @@ int ndiag_precision(const ndiag* h);
  *          (double for FP64, float otherwise). x_new must not alias x_old:
  *          a sweep reads old values of neighbouring subdomains (the halo of
  *          Sec. 3 "Data structure") while they are being overwritten.
- * Asynchronous on the handle's stream.
+ * Asynchronous on the handle's stream. Errors: NDIAG_EINVAL (a null pointer,
+ * x_new == x_old, unknown mode), NDIAG_EDEVICE.
  */
 ndiag_status sor_sweep(ndiag* h, int mode, const double* omega, int64_t t, const void* b,
                        const void* x_old, void* x_new);
@@ -133,6 +137,9 @@ ndiag_status sor_sweep(ndiag* h, int mode, const double* omega, int64_t t, const
  * J = implicit set of the forward phase (the phase at which subdomain 0
  * sweeps from the origin corner; with one subdomain this is classical SSOR).
  *   r, z  DEVICE vectors (handle precision), z must not alias r.
+ * Asynchronous on the handle's stream. Errors: NDIAG_EINVAL (a null pointer,
+ * z == r, unknown mode, omega outside (0, 2), a 9-point handle: its
+ * transposed sweep is not provided), NDIAG_EDEVICE.
  */
 ndiag_status ssor_apply(ndiag* h, int mode, double omega, const void* r, void* z);
 

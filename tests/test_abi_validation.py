@@ -171,3 +171,14 @@ def test_constructors_reject_bad_arguments(lib):
         out = P(1)
         st = lib.eikonal_create(C.byref(out), C.cast(nn, P), h, f.ctypes.data, C.cast(ss, P), None)
         assert st == EINVAL and out.value is None, (h, sub)
+
+
+def test_create_without_a_device_fails_loudly(lib):
+    # No CPU fallback: a valid matrix on a machine without a CUDA device is
+    # refused with NDIAG_EDEVICE and the CUDA error in ndiag_last_error().
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    st, h = _create(lib, 2, (6, 5), 5, (2, 1))
+    assert st == 5 and h is None  # NDIAG_EDEVICE
+    assert lib.ndiag_last_error().startswith(b"cudaGetDevice")
