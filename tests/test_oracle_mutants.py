@@ -15,6 +15,7 @@ from paper_1008_3699_gb300 import workloads as W
 from tests.oracle_dense import assemble, full_n, jmask_bool, neighbours
 from tests.test_oracle_sweep_sets import face_sets_hold, reflected_blocks_hold
 from tests.test_oracle_tables6to8 import decomposed_within_table6
+from tests.test_oracle_procedural2d import procedure_holds
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.cpp")
 
@@ -202,22 +203,26 @@ def pin_full_apply(L):
     return np.max(np.abs(M @ pb.ilu0_apply(r) - r)) <= 1e-12 * np.max(np.abs(r))
 
 
+def pin_procedure(L):
+    return procedure_holds((13, 11), (3, 2), L)
+
+
 MUTANTS = [
     ("no interface coupling",
      "  return q_up_in_i && i_up_in_q;", "  return false;",
-     [pin_table1_pgs2, pin_printed_systems, decomposed_within_table6]),
+     [pin_table1_pgs2, pin_printed_systems, decomposed_within_table6, pin_procedure]),
     ("1D starts outward",
      "  if (d == 1) return (int)(t & 1);", "  if (d == 1) return (int)((t + 1) & 1);",
      [pin_table1_pgs2]),
     ("2D pair order swapped",
      "  int c = all ^ (tt >> 1);", "  int c = all ^ (tt >> 1) ^ ((tt >> 1) ? 3 : 0);",
-     [pin_schedule, pin_printed_systems]),
+     [pin_schedule, pin_printed_systems, pin_procedure]),
     ("sign of the old-value term",
      "      if (j >= 0) acc -= wi * aval(pb, k, i) * u[j];", "      if (j >= 0) acc += wi * aval(pb, k, i) * u[j];",
-     [pin_splitting]),
+     [pin_splitting, pin_procedure]),
     ("dropped (1-w) D u term",
      "    double acc = (1.0 - wi) * aii * u[i] + wi * b[i];", "    double acc = wi * b[i];",
-     [pin_splitting]),
+     [pin_splitting, pin_procedure]),
     ("transposed solve uses the row's own entry",
      "          coef = (scale ? scale[j] : 1.0) * ent(kb, j);",
      "          coef = (scale ? scale[i] : 1.0) * ent(k, i);",
@@ -251,10 +256,10 @@ MUTANTS = [
      [lambda L: pin_krylov_counts(L, "pcg")]),
     ("relaxation factor of the opposite direction",
      "    const double wi = omega[pl.corner[i]];", "    const double wi = omega[pl.corner[i] ^ 1];",
-     [pin_table5_ssour]),
+     [pin_table5_ssour, pin_procedure]),
     ("lexicographic order reversed",
      "    if (kq != ki) return kq < ki;", "    if (kq != ki) return kq > ki;",
-     [pin_table1_pgs2, pin_printed_systems]),
+     [pin_table1_pgs2, pin_printed_systems, pin_procedure]),
     ("9-point diagonal across an interface taken as new when upstream",
      "  if (nz != 1) return false;  // diagonal neighbour across an interface: old value",
      "  if (nz != 1) return precedes(cq, ci, csi);",
