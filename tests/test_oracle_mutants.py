@@ -15,7 +15,7 @@ from paper_1008_3699_gb300 import workloads as W
 from tests.oracle_dense import assemble, full_n, jmask_bool, neighbours
 from tests.test_oracle_sweep_sets import face_sets_hold, reflected_blocks_hold
 from tests.test_oracle_tables6to8 import decomposed_within_table6
-from tests.test_oracle_procedural2d import procedure_holds
+from tests.test_oracle_procedure import procedure3d_holds, procedure_holds
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.cpp")
 
@@ -207,6 +207,10 @@ def pin_procedure(L):
     return procedure_holds((13, 11), (3, 2), L)
 
 
+def pin_procedure3d(L):
+    return procedure3d_holds((6, 5, 7), (2, 2, 3), L)
+
+
 MUTANTS = [
     ("no interface coupling",
      "  return q_up_in_i && i_up_in_q;", "  return false;",
@@ -271,6 +275,10 @@ MUTANTS = [
      "          if (pl.jmask[j] >> kb & 1) continue;  // mutual pair: no elimination term",
      "          if (pl.jmask[j] >> kb & 1) continue;  // mutual pair: no elimination term\n          if (k >= 5) continue;",
      [pin_dilu9]),
+    ("3D neighbours along z sweep the same way",
+     "  for (int a = 0; a < d; ++a)\n    if (idx[a] & 1) c ^= (1 << a);",
+     "  for (int a = 0; a < d && a < 2; ++a)\n    if (idx[a] & 1) c ^= (1 << a);",
+     [pin_procedure3d]),
 ]
 
 

@@ -1,5 +1,6 @@
-"""The oracle's decomposed 2D 5-point sweep against the procedure of Sec. 3,
-written out step by step in plain Python (no implicit sets, no dependency
+"""The oracle's decomposed 2D 5-point sweep against the procedure of Sec. 3
+(and the 3D 7-point sweep against Sec. 4, at the end of the file), written out
+step by step in plain Python (no implicit sets, no dependency
 graph):
 
 1. the start corners: subdomains whose start corners meet at one grid vertex
@@ -207,3 +208,157 @@ def test_corner_groups_have_the_printed_sizes():
             assert subs[iy * 3 + ix]["cs"] ^ subs[iy * 3 + ix + 1]["cs"] == 1
         for iy, ix in itertools.product(range(2), range(3)):
             assert subs[iy * 3 + ix]["cs"] ^ subs[(iy + 1) * 3 + ix]["cs"] == 2
+
+
+# ---------------------------------------------------------------------------
+# 3D (Sec. 4): the same procedure for the 7-point stencil
+# ---------------------------------------------------------------------------
+
+OFF3 = {1: (-1, 0, 0), 2: (1, 0, 0), 3: (0, -1, 0), 4: (0, 1, 0), 5: (0, 0, -1), 6: (0, 0, 1)}
+
+
+def base_corner_3d(t):
+    """Start corner of subdomain (0,0,0) at phase t: within each pair of sweeps
+    the direction reverses; pair g starts from the all-ones corner with the
+    bits of g flipped on x and y (the 3D schedule, which the paper leaves
+    open)."""
+    g = (t // 2) % 4
+    c = 7 ^ (g & 1) ^ (((g >> 1) & 1) << 1)
+    return c ^ 7 if t % 2 else c
+
+
+def procedural_sweep_3d(n, sub, d, omega, t, b, u):
+    """Sec. 4 in the form that needs no case list: every subdomain visits its
+    cells in lexicographic (z, y, x) order of its reflected frame; a cell that
+    lies on start faces with a neighbouring subdomain behind them is solved
+    together with the cells facing it across those faces (all subdomains
+    around a start vertex, edge or face start there): 8 cells at an interior
+    start vertex (the 8x8 system), 4 along a start edge, 2 across a start
+    face, 1 inside. A coupled group is solved once, when its first member is
+    reached; a cell's own subdomain supplies new values for the cells it has
+    visited, everything else is old."""
+    nx, ny, nz = n
+    A = d.reshape(7, nz, ny, nx)
+    uo = u.reshape(nz, ny, nx)
+    bb = b.reshape(nz, ny, nx)
+    parts = [_split(n[a], sub[a]) for a in range(3)]
+    subs = []
+    for iz, (z0, z1) in enumerate(parts[2]):
+        for iy, (y0, y1) in enumerate(parts[1]):
+            for ix, (x0, x1) in enumerate(parts[0]):
+                cs = base_corner_3d(t) ^ (ix & 1) ^ ((iy & 1) << 1) ^ ((iz & 1) << 2)
+                subs.append(dict(lo=(x0, y0, z0), hi=(x1, y1, z1), cs=cs, w=omega[cs]))
+    owner = {}
+    for s in subs:
+        for c in itertools.product(*(range(s["lo"][a], s["hi"][a]) for a in range(3))):
+            owner[c] = s
+    new = {}
+
+    def cell(s, r):
+        return tuple(s["hi"][a] - 1 - r[a] if s["cs"] >> a & 1 else s["lo"][a] + r[a] for a in range(3))
+
+    def nb(c, k):
+        q = tuple(c[a] + OFF3[k][a] for a in range(3))
+        return q if all(0 <= q[a] < n[a] for a in range(3)) else None
+
+    def solve(cells):
+        idx = {c: i for i, c in enumerate(cells)}
+        m = len(cells)
+        M = np.zeros((m, m))
+        r = np.zeros(m)
+        for i, c in enumerate(cells):
+            x, y, z = c
+            w = owner[c]["w"]
+            M[i, i] = A[0, z, y, x]
+            r[i] = (1 - w) * A[0, z, y, x] * uo[z, y, x] + w * bb[z, y, x]
+            for k in range(1, 7):
+                q = nb(c, k)
+                if q is None:
+                    continue
+                a = A[k, z, y, x]
+                if q in idx:
+                    M[i, idx[q]] += w * a
+                else:
+                    own = owner[q] is owner[c] and q in new
+                    r[i] -= w * a * (new[q] if own else uo[q[2], q[1], q[0]])
+        v = np.linalg.solve(M, r) if m > 1 else r / M[0, 0]
+        for c, val in zip(cells, v):
+            new[c] = val
+
+    for s in subs:
+        ext = [s["hi"][a] - s["lo"][a] for a in range(3)]
+        for rz, ry, rx in itertools.product(range(ext[2]), range(ext[1]), range(ext[0])):
+            c = cell(s, (rx, ry, rz))
+            if c in new:
+                continue
+            # the start faces this cell lies on that have a subdomain behind them
+            steps = []
+            for a, ra in enumerate((rx, ry, rz)):
+                if ra == 0:
+                    q = list(c)
+                    q[a] += 1 if s["cs"] >> a & 1 else -1
+                    if 0 <= q[a] < n[a]:
+                        steps.append((a, q[a] - c[a]))
+            group = []
+            for m in range(len(steps) + 1):
+                for sel in itertools.combinations(steps, m):
+                    q = list(c)
+                    for a, dlt in sel:
+                        q[a] += dlt
+                    group.append(tuple(q))
+            solve(sorted(group))
+    out = np.empty(nx * ny * nz)
+    for (x, y, z), v in new.items():
+        out[x + nx * (y + ny * z)] = v
+    assert len(new) == nx * ny * nz
+    return out
+
+
+PARTS3 = [((6, 5, 7), (2, 2, 3)), ((5, 4, 6), (5, 1, 2)), ((7, 6, 5), (3, 2, 2)), ((4, 4, 4), (1, 1, 1)),
+          ((6, 6, 6), (2, 2, 2))]
+
+
+def _rand7(n, seed):
+    g = np.random.default_rng(seed)
+    N = int(np.prod(n))
+    d = -g.uniform(0.2, 1.0, size=(7, N))
+    d = W._zero_outside(d, n, 7)
+    d[0] = -d[1:].sum(axis=0) + g.uniform(0.05, 0.5, N)
+    return d
+
+
+def procedure3d_holds(n, sub, library=None):
+    """Every phase of the oracle's 3D sweep equals the procedure, to 1e-13."""
+    g = np.random.default_rng(7)
+    N = int(np.prod(n))
+    d = _rand7(n, 8)
+    pb = oracle.Problem(3, n, 7, d, sub, library=library)
+    omega = g.uniform(0.6, 1.8, size=8)
+    b, u = g.uniform(-1, 1, N), g.uniform(-1, 1, N)
+    for t in range(8):
+        got = pb.sor_sweep(oracle.DECOMPOSED, t, omega, b, u)
+        want = procedural_sweep_3d(n, sub, d, omega, t, b, u)
+        if np.max(np.abs(got - want)) > 1e-13 * np.max(np.abs(want)):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("n,sub", PARTS3)
+def test_3d_sweep_follows_the_procedure_of_sec4(orc, n, sub):
+    assert [orc.base_corner(3, t) for t in range(8)] == [base_corner_3d(t) for t in range(8)]
+    assert procedure3d_holds(n, sub)
+
+
+def test_3d_corner_system_is_8x8_with_32_nonzeros():
+    # 2 x 2 x 2 subdomains at t = 0 all start at the centre vertex: one group
+    # of 8 cells; each cell has 3 coupled neighbours in it, so the system has
+    # 8 diagonal + 24 off-diagonal = 32 nonzeros (Sec. 4).
+    n = (6, 6, 6)
+    cells = []
+    for iz, iy, ix in itertools.product(range(2), range(2), range(2)):
+        cs = base_corner_3d(0) ^ ix ^ (iy << 1) ^ (iz << 2)
+        lo = (3 * ix, 3 * iy, 3 * iz)
+        cells.append(tuple(lo[a] + (2 if cs >> a & 1 else 0) for a in range(3)))
+    assert len(set(cells)) == 8
+    adj = sum(1 for p in cells for q in cells if sum(abs(p[a] - q[a]) for a in range(3)) == 1)
+    assert 8 + adj == 32
